@@ -1,0 +1,377 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every check here compares the oracle with a statement that is independent of
+the formula the oracle implements: the moment conditions of the appendix
+(Eqs. a1a, a1b), the definitions behind the closed forms (Eqs. N2, N11),
+exactness of the stencils on polynomials, conservation and stationarity
+properties, hand-derived golden values, and the physics the paper validates
+(flat-interface equilibrium, Laplace law).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_12553_gb300 import workloads as W
+
+# D2Q9 as printed in Section 3.1 (velocity matrix and weights).
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
+CV = np.stack([CX, CY], 1)
+CS2 = 1.0 / 3.0
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__),
+                                    "golden")
+
+
+def _rand_params(rng, N, unit=False):
+    rho = np.ones(N) if unit else rng.uniform(0.5, 20.0, size=N)
+    sig = W.sample_sigma(rng, N)
+    return W.base_params(N, 8, 8, sig, rho=rho,
+                         tau=list(rng.uniform(0.6, 1.5, N - 1)),
+                         tau_g=rng.uniform(0.6, 1.5),
+                         mobility=list(rng.uniform(0.01, 0.2, N - 1)))
+
+
+# ---------------------------------------------------------------------------
+# Local equilibria and forcing: moment conditions of the appendix
+# ---------------------------------------------------------------------------
+
+def test_geq_moments_appendix_a1a():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        p = _rand_params(rng, 3)
+        p["rho0"] = rng.uniform(-2, 2)
+        pr, rho = rng.uniform(-1e-2, 1e-2), rng.uniform(0.5, 20)
+        u = rng.uniform(-0.1, 0.1, 2)
+        g = oracle.geq(p, pr, rho, u[0], u[1])
+        assert abs(g.sum() - p["rho0"]) < 1e-14 * (1 + abs(p["rho0"]))
+        np.testing.assert_allclose(CV.T @ g, rho * u, rtol=0, atol=1e-14 * rho)
+        M2 = np.einsum("k,ka,kb->ab", g, CV, CV)
+        np.testing.assert_allclose(M2, pr * np.eye(2) + rho * np.outer(u, u),
+                                   rtol=0, atol=1e-14 * rho)
+        M3 = np.einsum("k,ka,kb,kc->abc", g, CV, CV, CV)
+        d = np.eye(2)
+        want = rho * CS2 * (np.einsum("ab,c->abc", d, u)
+                            + np.einsum("ac,b->abc", d, u)
+                            + np.einsum("bc,a->abc", d, u))
+        np.testing.assert_allclose(M3, want, rtol=0, atol=1e-14 * rho)
+
+
+def test_force_distribution_moments_appendix_a1b():
+    """Sum G = u.grad rho; sum c G = F; sum cc G per Eq. a1b. The J~u term
+    enters through the symmetric tensor (c c - cs2 I), so only its
+    symmetric part survives the second moment."""
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        tg = rng.uniform(0.55, 2.0)
+        u, F, gr, J = (rng.uniform(-1, 1, 2) * s for s in (0.1, 1e-4, 1.0, 1e-3))
+        G = oracle.force_dist(tg, u, F, gr, J)
+        ugr = u @ gr
+        assert abs(G.sum() - ugr) < 1e-15
+        np.testing.assert_allclose(CV.T @ G, F, rtol=0, atol=1e-17)
+        M2 = np.einsum("k,ka,kb->ab", G, CV, CV)
+        Ju = np.outer(J, u) / (tg - 0.5)
+        want = (np.outer(u, F) + np.outer(F, u) + CS2 * np.outer(u, gr)
+                + CS2 * np.outer(gr, u) + CS2 * ugr * np.eye(2)
+                + 0.5 * (Ju + Ju.T))
+        np.testing.assert_allclose(M2, want, rtol=0, atol=1e-15)
+
+
+def test_ch_equilibrium_and_source_moments():
+    """Sum h^eq = phi, sum c h^eq = phi u, sum cc h^eq = cs2 a C I (the
+    moments behind Eq. N30); sum R = 0, sum c R = (1 - 1/(2 tau)) d(phi u)."""
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        a, phi, Ci = rng.uniform(0.1, 3), rng.uniform(-1, 1), rng.uniform(-1e-3, 1e-3)
+        u, up = rng.uniform(-0.1, 0.1, 2), rng.uniform(-0.1, 0.1, 2)
+        pp, tau = rng.uniform(-1, 1), rng.uniform(0.55, 2)
+        h = oracle.heq(a, phi, Ci, u)
+        assert abs(h.sum() - phi) < 1e-15
+        np.testing.assert_allclose(CV.T @ h, phi * u, rtol=0, atol=1e-16)
+        M2 = np.einsum("k,ka,kb->ab", h, CV, CV)
+        np.testing.assert_allclose(M2, CS2 * a * Ci * np.eye(2), rtol=0,
+                                   atol=1e-17)
+        R = oracle.source(tau, phi, u, pp, up)
+        assert abs(R.sum()) < 1e-17
+        np.testing.assert_allclose(CV.T @ R,
+                                   (1 - 0.5 / tau) * (phi * u - pp * up),
+                                   rtol=0, atol=1e-16)
+
+
+# ---------------------------------------------------------------------------
+# Local algebra: Eqs. N2, N12, N17, N18, N29 against their definitions
+# ---------------------------------------------------------------------------
+
+def _fractions(p, phi):
+    s = oracle.OracleSim(p)
+    c, rho, hf = s.local_fractions(phi)
+    s.close()
+    return c, rho, hf
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_fractions_definitions(N):
+    rng = np.random.default_rng(10 + N)
+    p = _rand_params(rng, N)
+    rt = np.array(p["rho"])
+    for _ in range(20):
+        c = rng.dirichlet(np.ones(N))
+        phi = oracle.phi_from_c(p, c)
+        # Eq. N12: varphi_i = rho_i - rho_N with rho_k = rho~_k c_k (Eq. N2)
+        vp = 0.5 * (rt[:-1] - rt[-1]) + 0.5 * (rt[:-1] + rt[-1]) * phi
+        np.testing.assert_allclose(vp, rt[:-1] * c[:-1] - rt[-1] * c[-1],
+                                   atol=1e-13)
+        c2, rho, _ = _fractions(p, phi)
+        np.testing.assert_allclose(c2, c, atol=1e-14)      # round trip
+        assert abs(c2.sum() - 1.0) < 1e-14                 # sum c_k = 1
+        assert abs(rho - rt @ c) < 1e-13 * rt.max()        # rho = sum rho_k
+
+
+@pytest.mark.parametrize("N", [3, 4, 5])
+def test_hfun_is_half_dH_dphi(N):
+    """Eq. N17 as printed equals (1/2) dH/dphi_i with H = sum c_k^2 (1-c_k)^2
+    (Eq. N11), c_k(phi) from Eq. N18: this is the reading that makes the
+    tanh profile of width sqrt(2) eta an equilibrium (see the flat-interface
+    test below)."""
+    rng = np.random.default_rng(20 + N)
+    p = _rand_params(rng, N)
+    for _ in range(10):
+        phi = oracle.phi_from_c(p, rng.dirichlet(np.ones(N)))
+        _, _, hf = _fractions(p, phi)
+
+        def H(ph):
+            c, _, _ = _fractions(p, ph)
+            return np.sum(c ** 2 * (1 - c) ** 2)
+
+        e = 1e-6
+        for i in range(N - 1):
+            d = np.zeros(N - 1)
+            d[i] = e
+            dH = (H(phi + d) - H(phi - d)) / (2 * e)
+            assert abs(hf[i] - 0.5 * dH) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Stencils (Eq. N31 and Eq. N40)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_stencils_exact_on_quadratics(scheme):
+    """Both the central (Eq. N31a/b) and the mixed (Eq. N40) differences are
+    second order, hence exact on quadratic fields away from the wrap."""
+    rng = np.random.default_rng(30)
+    nx, ny = 24, 20
+    p = W.base_params(3, nx, ny, 1e-3, grad_scheme=scheme)
+    s = oracle.OracleSim(p)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    a, b, c, d, e = rng.uniform(-1, 1, 5)
+    z = a * x * x + b * x * y + c * y * y + d * x + e * y
+    grad, lap = s.stencils(z)
+    sl = (slice(3, ny - 3), slice(3, nx - 3))
+    np.testing.assert_allclose(grad[0][sl], (2 * a * x + b * y + d)[sl], atol=1e-11)
+    np.testing.assert_allclose(grad[1][sl], (b * x + 2 * c * y + e)[sl], atol=1e-11)
+    np.testing.assert_allclose(lap[sl], 2 * a + 2 * c, atol=1e-11)
+    s.close()
+
+
+def test_central_gradient_sums_to_zero_periodic():
+    """The central scheme is a difference of shifted copies: its global sum
+    vanishes on a periodic grid (the global mass property noted after
+    Eq. N31)."""
+    rng = np.random.default_rng(31)
+    p = W.base_params(3, 13, 11, 1e-3)
+    s = oracle.OracleSim(p)
+    z = rng.standard_normal((11, 13))
+    grad, lap = s.stencils(z)
+    assert abs(grad[0].sum()) < 1e-12 and abs(grad[1].sum()) < 1e-12
+    assert abs(lap.sum()) < 1e-12
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# Mixing energy coefficients (Eqs. N14-N16, N36)
+# ---------------------------------------------------------------------------
+
+def _read_golden(name):
+    vals = {}
+    with open(f"{GOLDEN}/{name}") as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
+def test_lambda_golden_n3_equal_sigma():
+    g = _read_golden("lambda_n3_equal_sigma.txt")
+    p = W.base_params(3, 8, 8, g["sigma"], eta=g["eta"])
+    lam = oracle.lam(p)
+    assert abs(oracle.beta(p) ** 2 - g["beta2"]) < 1e-15
+    np.testing.assert_allclose(lam, [[g["lam11"], g["lam12"]],
+                                     [g["lam12"], g["lam22"]]], rtol=1e-12)
+    np.testing.assert_allclose(np.linalg.eigvalsh(lam),
+                               [g["eig_min"], g["eig_max"]], rtol=1e-12)
+
+
+@pytest.mark.parametrize("N,unit", [(3, True), (3, False), (4, False),
+                                    (5, True), (5, False)])
+def test_flat_interface_is_equilibrium(N, unit):
+    """For equal sigma, the tanh profile of width sqrt(2) eta between any two
+    phases is a continuum equilibrium of the model (Section 2): every C_i is
+    uniform across it. With a wide interface the discrete C_i must be flat
+    up to the O(dx^2 / w^2) stencil error; a dropped factor in Eq. N14,
+    N17, N18 or N36 leaves an O(1) residual."""
+    rng = np.random.default_rng(40 + N)
+    rho = np.ones(N) if unit else rng.uniform(1, 20, N)
+    eta = 6 * math.sqrt(2)          # width 12 lattice units
+    ny = 240
+    for (k, l) in [(0, 1), (0, N - 1), (N - 2, N - 1)]:
+        if k == l:
+            continue
+        c = np.zeros((N, ny, 4))
+        band = W._layer(ny, 4, ny / 4, 3 * ny / 4, eta)
+        c[k] = band
+        c[l] = 1 - band
+        p = W.base_params(N, 4, ny, 1e-3, rho=rho, eta=eta)
+        s = oracle.OracleSim(p)
+        s.init(c)
+        Cp = s.chemical_potential()
+        scale = oracle.beta(p) ** 2 / eta ** 2 * max(rho)
+        resid = np.abs(Cp - Cp[:, :1, :1]).max() / scale
+        assert resid < 2e-3, (k, l, resid)
+        s.close()
+
+
+def test_surface_tension_integral():
+    """Excess gradient energy of an equilibrium flat interface equals sigma:
+    integral of sum lambda_ij phi_i' phi_j' over the interface (Eq. N11 at
+    equipartition). Pairs with sigma > sigma_min relax to width
+    sqrt(2) eta sigma / sigma_min, the width used here."""
+    rng = np.random.default_rng(50)
+    N = 4
+    rho = rng.uniform(1, 10, N)
+    sig = W.sample_sigma(rng, N)
+    eta = 5 * math.sqrt(2)
+    p = W.base_params(N, 4, 8, sig, rho=rho, eta=eta)
+    lam = oracle.lam(p)
+    smin = min(sig[a, b] for a in range(N) for b in range(N) if a != b)
+    y = np.linspace(-400, 400, 160001)
+    dy = y[1] - y[0]
+    for k in range(N):
+        for l in range(k + 1, N):
+            w = math.sqrt(2) * eta * sig[k, l] / smin
+            ck = 0.5 + 0.5 * np.tanh(y / w)
+            c = np.zeros((len(y), N))
+            c[:, k], c[:, l] = ck, 1 - ck
+            phi = np.array([oracle.phi_from_c(p, cc) for cc in c[::100]])
+            dphi = np.gradient(phi, dy * 100, axis=0)
+            e = np.einsum("yi,ij,yj->y", dphi, lam, dphi).sum() * dy * 100
+            assert abs(e - sig[k, l]) / sig[k, l] < 1e-3, (k, l, e, sig[k, l])
+
+
+# ---------------------------------------------------------------------------
+# Whole-step properties
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("wall", [0, 1])
+def test_mass_conservation(wall):
+    """Sum_x phi_i (hence sum_x c_k) is invariant: collision keeps sum_k h_k
+    (sum h^eq = phi, sum R = 0) and streaming / bounce-back only moves
+    populations."""
+    w = W.random_smooth(7, 4, 23, 17, rho=[3.0, 1.0, 2.0, 5.0], wall_y=wall,
+                        amp_u=0.02, gravity=(0.0, -1e-5))
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0, w.u0)
+    m0 = s.moments()["phi"].sum((1, 2))
+    mass0, _, _ = s.diagnostics()
+    s.step(200)
+    m1 = s.moments()["phi"].sum((1, 2))
+    mass1, ke, _ = s.diagnostics()
+    np.testing.assert_allclose(m1, m0, rtol=0, atol=1e-13 * w.V)
+    np.testing.assert_allclose(mass1, mass0, rtol=1e-13)
+    assert math.isfinite(ke)
+    s.close()
+
+
+@pytest.mark.parametrize("wall", [0, 1])
+def test_quiescent_state_is_stationary(wall):
+    w = W.quiescent(4, 9, 7, frac=[0.1, 0.2, 0.3, 0.4], rho=[2, 1, 3, 7],
+                    wall_y=wall)
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0)
+    m0 = s.moments()
+    s.step(1000)
+    m = s.moments()
+    assert np.abs(m["u"]).max() <= 1e-18
+    for k in ("phi", "c", "p", "rho"):
+        assert np.ptp(m[k], axis=(-2, -1)).max() <= 1e-15
+    np.testing.assert_allclose(m["phi"], m0["phi"], atol=1e-15)
+    s.close()
+
+
+def test_uniform_flow_is_preserved():
+    """A uniform mixture moving at constant velocity stays at equilibrium:
+    u is kept and the fields stay uniform (Eq. N22_1 and streaming)."""
+    w = W.quiescent(3, 10, 6, frac=[0.2, 0.5, 0.3], rho=[1, 4, 2])
+    u0 = np.zeros((2, 6, 10))
+    u0[0], u0[1] = 0.03, -0.02
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0, u0)
+    s.step(300)
+    m = s.moments()
+    np.testing.assert_allclose(m["u"][0], 0.03, atol=1e-15)
+    np.testing.assert_allclose(m["u"][1], -0.02, atol=1e-15)
+    assert np.ptp(m["phi"], axis=(-2, -1)).max() <= 1e-14
+    s.close()
+
+
+def test_rho0_is_inert():
+    """rho_0 of Eq. 25 appears only in g_0, which enters neither u (c_0 = 0)
+    nor p (Eq. N23 sums k >= 1): outputs are bit-identical."""
+    w = W.random_smooth(8, 3, 12, 10, rho=[2.0, 1.0, 5.0], amp_u=0.01)
+    outs = []
+    for r0 in (0.0, 1.0, 7.0):
+        p = dict(w.params, rho0=r0)
+        outs.append(oracle.run(p, w.c0, w.u0, steps=50))
+    for o in outs[1:]:
+        for k in ("phi", "u", "p"):
+            assert np.array_equal(o[k], outs[0][k])
+
+
+def test_flat_interface_stays_put():
+    """Equal sigma, N = 3, two flat 1|2 tanh interfaces: the profile moves
+    only by the stencil error, which falls at least as dx^2 / w^2 when the
+    width doubles (drift 4.4e-3 at W = 4 and 3.3e-4 at W = 8 after 2000
+    steps when this pin was written)."""
+    drifts = []
+    for mult in (1, 2):
+        w = W.flat_interface(N=3, nx=4, ny=64 * mult, steps=2000,
+                             eta=math.sqrt(2) * mult)
+        s = oracle.OracleSim(w.params)
+        s.init(w.c0)
+        s.step(w.steps)
+        drifts.append(np.abs(s.moments()["c"] - w.c0).max())
+        s.close()
+    assert drifts[0] < 1e-2 and drifts[1] < 1e-3, drifts
+    assert drifts[0] / drifts[1] > 4.0, drifts
+
+
+def test_laplace_law():
+    """Static drop: pressure jump sigma / R in 2-D (Section 4.1) within 5% at
+    W = 4, R = 12 after 8000 steps (finite-interface and finite-time error)."""
+    n, R, sig = 64, 12.0, 1e-3
+    w = W.static_drops(nx=n, ny=n, R=R, centres=((n / 2, n / 2), (0, 0)),
+                       N=3, sigma=sig)
+    w.c0[2] = 0.0
+    w.c0[0] = 1.0 - w.c0[1]
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0)
+    s.step(8000)
+    m = s.moments()
+    y, x = np.mgrid[0:n, 0:n]
+    r = np.hypot(x - n / 2, y - n / 2)
+    dp = m["p"][r < R / 2].mean() - m["p"][(m["c"][0] > 0.999) & (r > R + 12)].mean()
+    assert abs(dp / (sig / R) - 1) < 0.05, dp / (sig / R)
+    s.close()
