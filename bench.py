@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Throughput of the N-phase phase-field LB time step on one GB300.
+
+Workload: N = 5 phases on a 2048 x 2048 periodic D2Q9 grid (two horizontal
+tanh interfaces stacking phases 1-3 plus 16 seeded drops of phases 4-5,
+seeded sigma in [5e-4, 2e-3], M = 0.05, tau = 0.7), FP32 storage. A step is
+one time step of the whole grid (one fused kernel launch). Metric: MLUPS =
+node updates per second, each update advancing all N LB equations.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the
+method's grid is not sharded here): value = sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (node updates per second, all N LB equations)"
+WORKLOAD = ("N=5 droplets and interfaces, D2Q9 2048x2048 periodic, "
+            "FP32 storage")
+SEED = 4
+BYTES_PER_VALUE = {"fp64": (8, 8), "fp32": (4, 4), "bf16": (2, 4),
+                   "fp16": (2, 4)}
+
+
+def alg_bytes_per_node(N: int, prec: str) -> int:
+    """Algorithmic bytes per node-step: read + write of 9(N-1) h + 8 g +
+    (N-1) phi_prev + 2 u_prev; the 8N moving populations in the storage
+    type, the N-1 rest slots and the N+1 state values in the arithmetic
+    type."""
+    s_mov, s_rest = BYTES_PER_VALUE[prec]
+    return 2 * (8 * N * s_mov + (N - 1) * s_rest + (N + 1) * s_rest)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel_tag: str):
+    """Per-launch DRAM bytes recorded from an ncu capture of this kernel
+    (profiles/traffic.txt, `tag = bytes`), or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                line = line.split("#")[0].strip()
+                if "=" in line:
+                    k, v = line.split("=", 1)
+                    if k.strip() == kernel_tag:
+                        return float(v)
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while alive."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.samples = []
+        self.proc = None
+        self.window = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        t0, t1 = self.window or (0, 1e30)
+        sel = [s for (t, s) in self.samples if t0 - 0.05 <= t <= t1 + 0.05]
+        sel = sel or [s for (_, s) in self.samples]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for s in sel:
+            parts = [x.strip() for x in s.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sel)}
+
+
+def accept_sigma(N):
+    """sigma draws whose lambda (from the library's host setup) is well
+    conditioned: smallest eigenvalue > 1e-3 largest."""
+    from paper_1904_12553_gb300 import LbmError, lbm_nphase_derive, workloads as W
+
+    def ok(sig):
+        try:
+            d = lbm_nphase_derive(W.base_params(sig.shape[0], 4, 4, sig))
+        except LbmError:
+            return False
+        return d["lambda_eig_min"] > 1e-3 * d["lambda_eig_max"]
+    return ok
+
+
+def make_workload(prec="fp32", n=2048, accept=None):
+    from paper_1904_12553_gb300 import workloads as W
+    return W.droplets_interfaces(seed=SEED, n=n, precision=prec,
+                                 accept=accept)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def time_form(w, prec, steps, warmup, dist=None):
+    """Device time of `steps` back-to-back time steps (CUDA events on the
+    solver's stream), max over ranks."""
+    import torch
+    from paper_1904_12553_gb300 import Solver
+
+    s = Solver({**w.params, "precision": prec})
+    s.init(w.c0, w.u0, w.p0)
+    for _ in range(warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    e0.record(s.stream)
+    for _ in range(steps):
+        s.step(1)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mass, ke, _ = s.diagnostics()
+    s.close()
+    return ms, (wall0, wall1), mass, ke
+
+
+def e2e_run(w, prec, steps):
+    """Whole job through the C ABI with host buffers: H2D of the initial
+    fields from pinned memory (inside lbm_nphase_init), the steps, and the
+    D2H of phi, c, u, p, rho into pinned memory (lbm_nphase_moments)."""
+    import torch
+    from paper_1904_12553_gb300 import (Solver, lbm_nphase_init,
+                                        lbm_nphase_moments, lbm_nphase_step)
+
+    s = Solver({**w.params, "precision": prec})
+    N, V = s.N, s.V
+    c_host = torch.from_numpy(w.c0).pin_memory()
+    outs = {k: torch.empty(n * V, dtype=torch.float64).pin_memory()
+            for k, n in (("phi", N - 1), ("c", N), ("u", 2), ("p", 1),
+                         ("rho", 1))}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm_nphase_init(s.handle, c_host.data_ptr(), None, w.p0)
+    for _ in range(steps):
+        lbm_nphase_step(s.handle, 1)
+    lbm_nphase_moments(s.handle, outs["phi"].data_ptr(), outs["c"].data_ptr(),
+                       outs["u"].data_ptr(), outs["p"].data_ptr(),
+                       outs["rho"].data_ptr())
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    s.close()
+    h2d = N * V * 8
+    d2h = (2 * N + 3) * V * 8
+    return V * steps / t / 1e6, h2d / steps, d2h / steps
+
+
+def cpu_baseline(steps=3):
+    """The FP64 oracle on the full workload, timed on this host's cores in a
+    fresh process (OpenMP over rows, all cores)."""
+    cores = os.cpu_count() or 1
+    code = (
+        "import sys, time, json\n"
+        f"sys.path.insert(0, {ROOT!r}); sys.path.insert(0, {os.path.join(ROOT, 'oracle')!r})\n"
+        "import numpy as np, oracle\n"
+        "from paper_1904_12553_gb300 import workloads as W\n"
+        "def ok(sig):\n"
+        "    ev = np.linalg.eigvalsh(oracle.lam(W.base_params(5, 4, 4, sig)))\n"
+        "    return ev[0] > 1e-3 * ev[-1]\n"
+        f"w = W.droplets_interfaces(seed={SEED}, n=2048, precision='fp64', accept=ok)\n"
+        "s = oracle.OracleSim(w.params); s.init(w.c0)\n"
+        "s.step(1)\n"
+        "t = time.perf_counter()\n"
+        f"s.step({steps})\n"
+        "t = time.perf_counter() - t\n"
+        f"print(json.dumps({{'seconds': t, 'mlups': w.V * {steps} / t / 1e6}}))\n")
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True,
+                       text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        return {"value": None, "unit": "MLUPS", "cores": cores,
+                "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["mlups"], "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 oracle, {steps} time steps of the full "
+                      f"2048x2048 N=5 grid after one untimed step "
+                      f"({d['seconds']:.1f} s)"}
+
+
+def run_ours(args, dist, rank, world):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1904_12553_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    w = make_workload("fp32", accept=accept_sigma(5))
+    N, V = w.params["N"], w.V
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms, (wa, wb), mass, ke = time_form(w, "fp32", args.steps, args.warmup,
+                                       dist)
+    if sampler:
+        sampler.mark(wa, wb)
+    clocks = sampler.stop() if sampler else None
+    ms_step = ms / args.steps
+    value = world * V * args.steps / (ms / 1e3) / 1e6
+    if rank != 0:
+        return
+    peak, peak_kind = peaks()
+    B = alg_bytes_per_node(N, "fp32")
+    achieved = B * V / (ms_step / 1e3) / 1e9
+    forms = {}
+    if not args.quick:
+        for prec, k in (("bf16", args.steps), ("fp16", args.steps),
+                        ("fp64", max(10, args.steps // 20))):
+            fms, _, fmass, _ = time_form(w, prec, k, min(args.warmup, 5))
+            fstep = fms / k
+            fB = alg_bytes_per_node(N, prec)
+            forms[prec] = {
+                "mlups": V / (fstep / 1e3) / 1e6, "ms_per_step": fstep,
+                "alg_bytes_per_node": fB,
+                "hbm_frac": fB * V / (fstep / 1e3) / 1e9 / peak}
+    e2e_v, h2d, d2h = e2e_run(w, "fp32", args.steps)
+    cpu = cpu_baseline() if (world == 1 and not args.quick) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded initial condition)",
+        "config": {"workload": WORKLOAD, "N": N, "nx": w.params["nx"],
+                   "ny": w.params["ny"], "precision": "fp32", "seed": SEED,
+                   "l2": "state (%.2f GB) larger than L2, no flush"
+                         % (B / 2 * V / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind,
+                     "alg_bytes_per_node": B,
+                     "traffic": traffic_from_profiles("tile_kernel_fp32_n5_2048")},
+        "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "forms": forms,
+        "check": {"mass": list(map(float, mass)), "ke": float(ke)},
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    cores = os.cpu_count() or 1
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    import numpy as np
+    import oracle
+    from paper_1904_12553_gb300 import workloads as W
+
+    def ok(sig):
+        ev = np.linalg.eigvalsh(oracle.lam(W.base_params(5, 4, 4, sig)))
+        return ev[0] > 1e-3 * ev[-1]
+
+    # Each step: one oracle time step on an n x n window of the workload,
+    # n chosen so that all warm-up and timed steps take about two minutes.
+    probe = W.droplets_interfaces(seed=SEED, n=256, precision="fp64",
+                                  accept=ok)
+    s = oracle.OracleSim(probe.params)
+    s.init(probe.c0)
+    t = time.perf_counter()
+    s.step(2)
+    rate = 2 * probe.V / (time.perf_counter() - t)
+    s.close()
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    n = int(math.sqrt(rate * per_step))
+    n = max(64, min(2048, n - n % 32))
+    w = W.droplets_interfaces(seed=SEED, n=n, precision="fp64", accept=ok,
+                              ndrops=max(1, int(16 * (n / 2048) ** 2)))
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0)
+    s.step(args.warmup)
+    t = time.perf_counter()
+    s.step(args.steps)
+    sec = time.perf_counter() - t
+    s.close()
+    value = w.V * args.steps / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded initial condition)",
+        "config": {"workload": WORKLOAD, "N": 5, "nx": 2048, "ny": 2048,
+                   "precision": "fp32", "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"FP64 oracle time steps on a {n}x{n} "
+                                   "window of the workload, one per step"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the other storage forms and the CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl")
+        dist = dist_
+    try:
+        run_ours(args, dist, rank, world)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

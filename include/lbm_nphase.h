@@ -1,0 +1,161 @@
+/*
+ * lbm_nphase.h -- C ABI of the GB300 (sm_103a) phase-field lattice Boltzmann
+ * solver for immiscible incompressible N-phase flow, after Yuan, Liang, Chai
+ * and Shi, "Phase-field-based lattice Boltzmann model for immiscible
+ * incompressible N-phase flows" (arXiv:1904.12553).
+ *
+ * One handle owns one D2Q9 grid of nx x ny nodes with N phases (2 <= N <= 5):
+ * N-1 Cahn-Hilliard distributions h^i_k (Eq. N24) and one Navier-Stokes
+ * distribution g_k (Eq. 24) per node. A time step computes the chemical
+ * potentials C_i from the isotropic stencils of Eq. N31, the total force
+ * F = sum_i C_i grad(phi_i) + G, the moments u (Eq. N22_1) and p (Eq. N23),
+ * the collisions with the equilibria of Eqs. 25 and N25, the total-force
+ * distribution of Eq. N20_1 and the source of Eqs. N26-N27, and streams the
+ * populations. Lattice units: dx = dt = 1, c_s^2 = 1/3.
+ *
+ * Conventions for every function below:
+ *  - Arrays are row-major [field][y][x] with x fastest, FP64, node (x, y) at
+ *    integer coordinates. Field order: phases 1..N (the paper's indices).
+ *  - Device work is ordered on the CUDA stream given to lbm_nphase_create
+ *    (NULL = the legacy default stream). lbm_nphase_step is asynchronous;
+ *    lbm_nphase_init, lbm_nphase_moments and lbm_nphase_diagnostics return
+ *    after their results are complete (they synchronise the stream).
+ *  - A handle is not thread safe. The library never frees caller memory; the
+ *    workspace must outlive the handle.
+ *  - Functions never abort or exit; they return an lbm_status. After
+ *    LBM_EUNSTABLE the handle refuses lbm_nphase_step (LBM_ESTATE) until
+ *    lbm_nphase_init is called again.
+ */
+#ifndef LBM_NPHASE_H
+#define LBM_NPHASE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_N 5
+
+typedef struct lbm_nphase_t lbm_nphase_t; /* opaque; owns all device state */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* invalid argument or parameter set */
+  LBM_ENOMEM = 2,    /* workspace too small */
+  LBM_ECUDA = 3,     /* a CUDA call failed (see lbm_nphase_cuda_error) */
+  LBM_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  LBM_EUNSTABLE = 5, /* non-finite mass or kinetic energy detected */
+  LBM_ESTATE = 6     /* call not valid in the handle's current state */
+} lbm_status;
+
+typedef enum {
+  LBM_FP64 = 0,     /* FP64 storage and arithmetic */
+  LBM_FP32 = 1,     /* FP32 storage and arithmetic */
+  LBM_MIX_BF16 = 2, /* moving populations stored as BF16 f_k/w_k * s, FP32 math */
+  LBM_MIX_FP16 = 3  /* moving populations stored as FP16 f_k/w_k * s, FP32 math */
+} lbm_precision;
+
+/* Model parameters, as the paper states them (Sections 2-4). */
+typedef struct {
+  int32_t N;           /* number of phases, 2..5 */
+  int32_t nx, ny;      /* grid size, >= 1 each */
+  int32_t wall_y;      /* 0: periodic in y; 1: halfway bounce-back walls at
+                          y = -1/2 and y = ny - 1/2 (Section 4.2). x is
+                          always periodic. */
+  int32_t precision;   /* lbm_precision */
+  int32_t grad_scheme; /* 0: isotropic central scheme, Eq. N31a (the only
+                          value accepted) */
+  double rho[LBM_MAX_N];              /* pure-phase densities rho~_k > 0 */
+  double sigma[LBM_MAX_N][LBM_MAX_N]; /* pairwise surface tensions sigma_kl
+                                         > 0, symmetric; diagonal ignored */
+  double eta;          /* interface thickness; tanh profile width sqrt(2) eta */
+  double beta;         /* <= 0: beta = sqrt(3 sqrt(2) sigma_min eta), Eq. N36 */
+  double tau_g;        /* NS relaxation time > 1/2; nu = (tau_g - 1/2)/3, Eq. N21_1 */
+  double tau[LBM_MAX_N - 1];      /* CH relaxation times tau_i > 1/2 */
+  double mobility[LBM_MAX_N - 1]; /* m_i > 0; a_i = m_i / (c_s^2 (tau_i - 1/2)), Eq. N30 */
+  double gravity[2];   /* body force G = rho * gravity */
+  double rho0;         /* constant of g_0^eq (Eq. 25); it affects no output */
+} lbm_nphase_params;
+
+/* Constants derived on the host from the parameters. */
+typedef struct {
+  double lambda[LBM_MAX_N - 1][LBM_MAX_N - 1]; /* lambda_ij, Eqs. N14-N16 */
+  double lambda_eig_min, lambda_eig_max;       /* extreme eigenvalues */
+  double beta;                                 /* Eq. N36 or given */
+  double a[LBM_MAX_N - 1];                     /* a_i of Eq. N30 */
+  double Gamma;                                /* sum 1/rho~_k, Eq. N1 */
+  double nu;                                   /* Eq. N21_1 */
+  int32_t uniform_density;                     /* 1 if all rho~_k are equal */
+  int32_t pad_;
+} lbm_nphase_model;
+
+/* Validate a parameter set and derive its constants on the host (no GPU
+ * needed). lambda comes from the N(N-1)/2 equations of Eq. N14 with the
+ * coefficients of Eqs. N15/N16. Returns LBM_EINVAL if a parameter is out of
+ * range, sigma is not symmetric, or lambda is singular or not positive
+ * definite. `out` may be NULL (validation only). */
+lbm_status lbm_nphase_derive(const lbm_nphase_params *params,
+                             lbm_nphase_model *out);
+
+/* Bytes of device workspace a handle with these parameters needs (0 if the
+ * parameters are invalid). */
+size_t lbm_nphase_workspace_bytes(const lbm_nphase_params *params);
+
+/* Create a handle on the current CUDA device. `d_workspace` is caller-owned
+ * device memory of at least lbm_nphase_workspace_bytes() bytes, 256-byte
+ * aligned; `cuda_stream` is a cudaStream_t (NULL: default stream). No device
+ * computation happens here. Errors: LBM_EINVAL (parameters, NULL arguments,
+ * misaligned workspace), LBM_ENOMEM (workspace too small), LBM_ECUDA. */
+lbm_status lbm_nphase_create(const lbm_nphase_params *params,
+                             void *d_workspace, size_t workspace_bytes,
+                             void *cuda_stream, lbm_nphase_t **out);
+
+/* Initial state from volume fractions c[N][ny][nx] (Eq. N2, sum_k c_k = 1)
+ * and velocity u[2][ny][nx] (NULL: fluid at rest), uniform pressure p0.
+ * Pointers may be host or device memory. The order parameters follow from
+ * the inverse of Eqs. N2 and N12; the distributions start at equilibrium,
+ * h = h^eq(phi, C, u) (Eq. N25) and g = g^eq(p0, u) (Eq. 25), and the
+ * previous-step product of Eq. N27 starts at phi u. Synchronises. */
+lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
+                           double p0);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the handle's stream). Each
+ * step is one fused kernel: zeroth moments (Eq. N28), chemical potentials
+ * (Eqs. N17, N18, N31), forces, u and p (Eqs. N22_1, N23), both
+ * collisions (Eqs. 24, N24) and streaming. Errors: LBM_ESTATE before init or
+ * after LBM_EUNSTABLE, LBM_ECUDA. */
+lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps);
+
+/* Macroscopic fields at the current time: phi[N-1][ny][nx], c[N][ny][nx],
+ * u[2][ny][nx], p[ny][nx], rho[ny][nx] (Eqs. N28, N18, N22_1, N23, N29).
+ * Any pointer may be NULL; non-NULL pointers may be host or device memory.
+ * Synchronises. */
+lbm_status lbm_nphase_moments(lbm_nphase_t *h, double *phi, double *c,
+                              double *u, double *p, double *rho);
+
+/* FP64 conservation diagnostics at the current time, reduced on the GPU in a
+ * fixed order: mass[k] = sum_x c_k (N values), ke = 1/2 sum_x rho |u|^2,
+ * umax = max_x |u|. Host pointers; any may be NULL. Returns LBM_EUNSTABLE
+ * (and marks the handle) if a result is not finite. Synchronises. */
+lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
+                                  double *umax);
+
+/* Number of time steps taken since the last init. */
+int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
+
+/* The last CUDA error code seen by the handle (0 if none). */
+int lbm_nphase_cuda_error(const lbm_nphase_t *h);
+
+/* Release the handle (not the workspace). NULL is accepted. */
+lbm_status lbm_nphase_destroy(lbm_nphase_t *h);
+
+/* Static description of a status code. */
+const char *lbm_nphase_strerror(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_NPHASE_H */

@@ -1,0 +1,559 @@
+// C ABI of the N-phase phase-field lattice Boltzmann solver: parameter
+// validation, derived constants, workspace layout, and the host driver of
+// the kernels. The arithmetic of a time step lives in lbm_kernels.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm_internal.h"
+#include "lbm_nphase.h"
+
+using lbm::Consts;
+using lbm::Grid;
+using lbm::Outputs;
+
+struct lbm_nphase_t {
+  lbm_nphase_params prm;
+  lbm_nphase_model mdl;
+  Consts k;
+  Grid g;
+  int prec;
+  bool nonunif, wall;
+  cudaStream_t stream;
+  int device;
+  double *stage;  // (N + 2) * V doubles: host <-> device staging
+  int cur;        // buffer holding the state at the current time
+  bool initialized, unstable;
+  int64_t steps;
+  int cuda_err;
+};
+
+namespace {
+
+constexpr double CS2 = 1.0 / 3.0;
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// Coefficient of lambda_ij in the equation of pair (k, l): Eq. N15 (l = N)
+// and Eq. N16 (l < N), 0-based phases.
+double Lcoef(const lbm_nphase_params *p, int i, int k, int l) {
+  const int n = p->N - 1;
+  const double rN = p->rho[n];
+  if (l == n) return i == k ? 1.0 : rN / (p->rho[i] + rN);
+  if (i == k) return p->rho[k] / (p->rho[k] + rN);
+  if (i == l) return -p->rho[l] / (p->rho[l] + rN);
+  return 0.0;
+}
+
+// Least-squares-free square solve A x = b by Householder QR (m <= 10).
+// Returns false if R has a (relatively) vanishing diagonal entry.
+bool householder_solve(int m, double A[10][10], double b[10], double x[10]) {
+  double amax = 0.0;
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c) amax = fmax(amax, fabs(A[r][c]));
+  if (amax == 0.0) return false;
+  for (int c = 0; c < m; ++c) {
+    double nrm = 0.0;
+    for (int r = c; r < m; ++r) nrm += A[r][c] * A[r][c];
+    nrm = sqrt(nrm);
+    if (nrm <= 1e-13 * amax) return false;
+    const double alpha = A[c][c] > 0 ? -nrm : nrm;
+    double v[10];
+    for (int r = 0; r < m; ++r) v[r] = r < c ? 0.0 : A[r][c];
+    v[c] -= alpha;
+    double vv = 0.0;
+    for (int r = c; r < m; ++r) vv += v[r] * v[r];
+    if (vv == 0.0) continue;
+    for (int cc = c; cc < m; ++cc) {
+      double d = 0.0;
+      for (int r = c; r < m; ++r) d += v[r] * A[r][cc];
+      d = 2.0 * d / vv;
+      for (int r = c; r < m; ++r) A[r][cc] -= d * v[r];
+    }
+    double d = 0.0;
+    for (int r = c; r < m; ++r) d += v[r] * b[r];
+    d = 2.0 * d / vv;
+    for (int r = c; r < m; ++r) b[r] -= d * v[r];
+  }
+  for (int r = m - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int c = r + 1; c < m; ++c) s -= A[r][c] * x[c];
+    x[r] = s / A[r][r];
+  }
+  return true;
+}
+
+// Extreme eigenvalues of a symmetric n x n matrix (n <= 4), cyclic Jacobi.
+void sym_eig_range(int n, const double M[4][4], double *lo, double *hi) {
+  double a[4][4];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) a[i][j] = M[i][j];
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += a[i][j] * a[i][j];
+    if (off < 1e-40) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (a[p][q] == 0.0) continue;
+        const double th = 0.5 * atan2(2.0 * a[p][q], a[q][q] - a[p][p]);
+        const double c = cos(th), s = sin(th);
+        for (int r = 0; r < n; ++r) {
+          const double arp = a[r][p], arq = a[r][q];
+          a[r][p] = c * arp - s * arq;
+          a[r][q] = s * arp + c * arq;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double apr = a[p][r], aqr = a[q][r];
+          a[p][r] = c * apr - s * aqr;
+          a[q][r] = s * apr + c * aqr;
+        }
+      }
+  }
+  *lo = a[0][0];
+  *hi = a[0][0];
+  for (int i = 1; i < n; ++i) {
+    *lo = fmin(*lo, a[i][i]);
+    *hi = fmax(*hi, a[i][i]);
+  }
+}
+
+bool cholesky_ok(int n, const double M[4][4]) {
+  double L[4][4] = {{0}};
+  for (int j = 0; j < n; ++j) {
+    double d = M[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0)) return false;
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double s = M[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = s / L[j][j];
+    }
+  }
+  return true;
+}
+
+lbm_status validate(const lbm_nphase_params *p) {
+  if (!p) return LBM_EINVAL;
+  if (p->N < 2 || p->N > LBM_MAX_N) return LBM_EINVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nx > (1 << 20) || p->ny > (1 << 20))
+    return LBM_EINVAL;
+  if ((double)p->nx * (double)p->ny > 17179869184.0) return LBM_EINVAL;
+  if (p->wall_y != 0 && p->wall_y != 1) return LBM_EINVAL;
+  if (p->precision < LBM_FP64 || p->precision > LBM_MIX_FP16) return LBM_EINVAL;
+  if (p->grad_scheme != 0) return LBM_EINVAL;
+  for (int k = 0; k < p->N; ++k)
+    if (!finite_pos(p->rho[k])) return LBM_EINVAL;
+  for (int k = 0; k < p->N; ++k)
+    for (int l = k + 1; l < p->N; ++l) {
+      const double a = p->sigma[k][l], b = p->sigma[l][k];
+      if (!finite_pos(a) || !finite_pos(b)) return LBM_EINVAL;
+      if (fabs(a - b) > 1e-12 * fmax(a, b)) return LBM_EINVAL;
+    }
+  if (!finite_pos(p->eta)) return LBM_EINVAL;
+  if (!isfinite(p->beta)) return LBM_EINVAL;
+  if (!(isfinite(p->tau_g) && p->tau_g > 0.5)) return LBM_EINVAL;
+  for (int i = 0; i < p->N - 1; ++i) {
+    if (!(isfinite(p->tau[i]) && p->tau[i] > 0.5)) return LBM_EINVAL;
+    if (!finite_pos(p->mobility[i])) return LBM_EINVAL;
+  }
+  if (!isfinite(p->gravity[0]) || !isfinite(p->gravity[1]) ||
+      !isfinite(p->rho0))
+    return LBM_EINVAL;
+  return LBM_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t h0, hm, gm, phi_prev, u_prev, stage, red, red_out, total;
+};
+
+Layout layout(const lbm_nphase_params *p) {
+  const size_t V = (size_t)p->nx * p->ny;
+  const int NP = p->N - 1;
+  const size_t sT = p->precision == LBM_FP64 ? 8 : 4;
+  const size_t sS = p->precision == LBM_FP64 ? 8 : (p->precision == LBM_FP32 ? 4 : 2);
+  const size_t tiles = (size_t)lbm::tiles_x(p->nx) * lbm::tiles_y(p->ny);
+  Layout L;
+  size_t off = 0;
+  L.h0 = off;       off += 2 * align256(NP * V * sT);
+  L.hm = off;       off += 2 * align256(NP * 8 * V * sS);
+  L.gm = off;       off += 2 * align256(8 * V * sS);
+  L.phi_prev = off; off += align256(NP * V * sT);
+  L.u_prev = off;   off += align256(2 * V * sT);
+  L.stage = off;    off += align256((p->N + 2) * V * 8);
+  L.red = off;      off += align256(tiles * (p->N + 2) * 8);
+  L.red_out = off;  off += align256(8 * 8);
+  L.total = off;
+  return L;
+}
+
+bool is_device_ptr(const void *ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+lbm_status cuda_fail(lbm_nphase_t *h, cudaError_t e) {
+  h->cuda_err = (int)e;
+  return LBM_ECUDA;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// Deterministic second pass of the diagnostics reduction.
+// --------------------------------------------------------------------------
+__global__ void reduce_partials_kernel(const double *__restrict__ part,
+                                       int nparts, int nvals,
+                                       double *__restrict__ out) {
+  __shared__ double s[256];
+  const int t = threadIdx.x;
+  for (int j = 0; j < nvals; ++j) {
+    const bool is_max = j == nvals - 1;
+    double v = is_max ? 0.0 : 0.0;
+    for (int b = t; b < nparts; b += 256) {
+      const double x = part[(size_t)b * nvals + j];
+      v = is_max ? fmax(v, x) : v + x;
+    }
+    s[t] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (t < w) s[t] = is_max ? fmax(s[t], s[t + w]) : s[t] + s[t + w];
+      __syncthreads();
+    }
+    if (t == 0) out[j] = s[0];
+    __syncthreads();
+  }
+}
+
+namespace lbm {
+
+cudaError_t launch_tile(int prec, const Consts &k, const Grid &g, int cur,
+                        int mode, const Outputs &o, bool nonunif, bool wall,
+                        cudaStream_t s) {
+  switch (prec) {
+    case LBM_FP64: return launch_tile_f64(k, g, cur, mode, o, nonunif, wall, s);
+    case LBM_FP32: return launch_tile_f32(k, g, cur, mode, o, nonunif, wall, s);
+    case LBM_MIX_BF16: return launch_tile_bf16(k, g, cur, mode, o, nonunif, wall, s);
+    case LBM_MIX_FP16: return launch_tile_f16(k, g, cur, mode, o, nonunif, wall, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(int prec, const Consts &k, const Grid &g, int cur,
+                        const double *c, const double *u, double p0, bool wall,
+                        cudaStream_t s) {
+  switch (prec) {
+    case LBM_FP64: return launch_init_f64(k, g, cur, c, u, p0, wall, s);
+    case LBM_FP32: return launch_init_f32(k, g, cur, c, u, p0, wall, s);
+    case LBM_MIX_BF16: return launch_init_bf16(k, g, cur, c, u, p0, wall, s);
+    case LBM_MIX_FP16: return launch_init_f16(k, g, cur, c, u, p0, wall, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce(const Grid &g, int nparts, int nvals, cudaStream_t s) {
+  reduce_partials_kernel<<<1, 256, 0, s>>>(g.red, nparts, nvals, g.red_out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+// --------------------------------------------------------------------------
+// Public API
+// --------------------------------------------------------------------------
+extern "C" {
+
+const char *lbm_nphase_strerror(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "success";
+    case LBM_EINVAL: return "invalid argument or parameter set";
+    case LBM_ENOMEM: return "workspace too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ETIMEOUT: return "bounded device wait timed out";
+    case LBM_EUNSTABLE: return "non-finite mass or kinetic energy";
+    case LBM_ESTATE: return "call not valid in the current handle state";
+  }
+  return "unknown status";
+}
+
+lbm_status lbm_nphase_derive(const lbm_nphase_params *p, lbm_nphase_model *out) {
+  lbm_status st = validate(p);
+  if (st != LBM_OK) return st;
+  lbm_nphase_model m;
+  memset(&m, 0, sizeof(m));
+  const int N = p->N, n = N - 1;
+  double smin = INFINITY;
+  for (int k = 0; k < N; ++k)
+    for (int l = k + 1; l < N; ++l) smin = fmin(smin, p->sigma[k][l]);
+  m.beta = p->beta > 0.0 ? p->beta : sqrt(3.0 * sqrt(2.0) * smin * p->eta);
+  // Eq. N14: unknowns lambda_ij (i <= j), one equation per pair k < l.
+  int ui[10], uj[10], M = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) {
+      ui[M] = i;
+      uj[M] = j;
+      ++M;
+    }
+  double A[10][10], b[10], x[10];
+  int row = 0;
+  const double rhs = 4.5 * p->eta * p->eta / (m.beta * m.beta);
+  for (int k = 0; k < N; ++k)
+    for (int l = k + 1; l < N; ++l) {
+      for (int c = 0; c < M; ++c) {
+        const double Li = Lcoef(p, ui[c], k, l), Lj = Lcoef(p, uj[c], k, l);
+        A[row][c] = ui[c] == uj[c] ? Li * Li : 2.0 * Li * Lj;
+      }
+      b[row] = rhs * p->sigma[k][l] * p->sigma[k][l];
+      ++row;
+    }
+  if (!householder_solve(M, A, b, x)) return LBM_EINVAL;
+  for (int c = 0; c < M; ++c) {
+    m.lambda[ui[c]][uj[c]] = x[c];
+    m.lambda[uj[c]][ui[c]] = x[c];
+  }
+  double lam4[4][4] = {{0}};
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) lam4[i][j] = m.lambda[i][j];
+  if (!cholesky_ok(n, lam4)) return LBM_EINVAL;
+  sym_eig_range(n, lam4, &m.lambda_eig_min, &m.lambda_eig_max);
+  m.Gamma = 0.0;
+  for (int k = 0; k < N; ++k) m.Gamma += 1.0 / p->rho[k];
+  for (int i = 0; i < n; ++i) m.a[i] = p->mobility[i] / (CS2 * (p->tau[i] - 0.5));
+  m.nu = CS2 * (p->tau_g - 0.5);
+  m.uniform_density = 1;
+  for (int k = 1; k < N; ++k)
+    if (p->rho[k] != p->rho[0]) m.uniform_density = 0;
+  if (out) *out = m;
+  return LBM_OK;
+}
+
+size_t lbm_nphase_workspace_bytes(const lbm_nphase_params *p) {
+  if (validate(p) != LBM_OK) return 0;
+  return layout(p).total;
+}
+
+lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
+                             size_t bytes, void *stream, lbm_nphase_t **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  lbm_nphase_model m;
+  lbm_status st = lbm_nphase_derive(p, &m);
+  if (st != LBM_OK) return st;
+  if (!ws || ((uintptr_t)ws & 255u)) return LBM_EINVAL;
+  const Layout L = layout(p);
+  if (bytes < L.total) return LBM_ENOMEM;
+  lbm_nphase_t *h = new (std::nothrow) lbm_nphase_t;
+  if (!h) return LBM_ENOMEM;
+  memset((void *)h, 0, sizeof(*h));
+  h->prm = *p;
+  h->mdl = m;
+  h->prec = p->precision;
+  h->wall = p->wall_y != 0;
+  h->nonunif = !m.uniform_density;
+  h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return LBM_ECUDA;
+  }
+  const int N = p->N, n = N - 1;
+  Consts &k = h->k;
+  memset(&k, 0, sizeof(k));
+  k.N = N;
+  k.NP = n;
+  const double Gam = m.Gamma;
+  double gam[5];
+  for (int q = 0; q < N; ++q) gam[q] = 1.0 / p->rho[q];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) k.lam[i][j] = m.lambda[i][j];
+    k.a[i] = m.a[i];
+    k.tau_inv[i] = 1.0 / p->tau[i];
+    k.src[i] = 1.0 - 1.0 / (2.0 * p->tau[i]);
+    k.off[i] = 0.5 * (p->rho[i] - p->rho[n]);
+    k.mul[i] = 0.5 * (p->rho[i] + p->rho[n]);
+    k.K[i] = 1.0 - N * gam[i] / Gam;
+    k.kap[i] = k.K[i] * k.mul[i];
+    k.kmob[i] = k.kap[i] * p->mobility[i];
+  }
+  for (int q = 0; q < N; ++q) {
+    k.c0[q] = gam[q] / Gam;
+    for (int j = 0; j < n; ++j)
+      k.Q[q][j] = (q == j ? gam[q] : 0.0) - gam[q] * gam[j] / Gam;
+    k.rho_t[q] = p->rho[q];
+  }
+  k.bulk = m.beta * m.beta / (p->eta * p->eta);
+  k.tg_inv = 1.0 / p->tau_g;
+  k.ffac = 1.0 - 1.0 / (2.0 * p->tau_g);
+  k.jfac = 1.0 / (p->tau_g - 0.5);
+  k.grav[0] = p->gravity[0];
+  k.grav[1] = p->gravity[1];
+  k.rho_base = N / Gam;
+  // 16-bit storage: h_k / w_k and g_k / w_k are O(1e-4 .. 1e-1) for the
+  // model's parameter ranges; 2^12 keeps them in FP16's normal range.
+  k.sh = 4096.0;
+  k.sg = 4096.0;
+  Grid &g = h->g;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.V = (size_t)p->nx * p->ny;
+  char *base = (char *)ws;
+  const size_t sT = h->prec == LBM_FP64 ? 8 : 4;
+  const size_t sS = h->prec == LBM_FP64 ? 8 : (h->prec == LBM_FP32 ? 4 : 2);
+  const size_t h0b = align256(n * g.V * sT), hmb = align256(n * 8 * g.V * sS),
+               gmb = align256(8 * g.V * sS);
+  for (int b = 0; b < 2; ++b) {
+    g.h0[b] = base + L.h0 + b * h0b;
+    g.hm[b] = base + L.hm + b * hmb;
+    g.gm[b] = base + L.gm + b * gmb;
+  }
+  g.phi_prev = base + L.phi_prev;
+  g.u_prev = base + L.u_prev;
+  h->stage = (double *)(base + L.stage);
+  g.red = (double *)(base + L.red);
+  g.red_out = (double *)(base + L.red_out);
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
+                           double p0) {
+  if (!h || !c || !isfinite(p0)) return LBM_EINVAL;
+  const size_t V = h->g.V;
+  const int N = h->prm.N;
+  const double *dc = c, *du = u;
+  cudaError_t e;
+  if (!is_device_ptr(c)) {
+    e = cudaMemcpyAsync(h->stage, c, N * V * sizeof(double),
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    dc = h->stage;
+  }
+  if (u && !is_device_ptr(u)) {
+    e = cudaMemcpyAsync(h->stage + N * V, u, 2 * V * sizeof(double),
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    du = h->stage + N * V;
+  }
+  e = lbm::launch_init(h->prec, h->k, h->g, 0, dc, du, p0, h->wall, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->cur = 0;
+  h->steps = 0;
+  h->initialized = true;
+  h->unstable = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps) {
+  if (!h || nsteps < 0) return LBM_EINVAL;
+  if (!h->initialized || h->unstable) return LBM_ESTATE;
+  const Outputs none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int64_t t = 0; t < nsteps; ++t) {
+    cudaError_t e = lbm::launch_tile(h->prec, h->k, h->g, h->cur,
+                                     lbm::MODE_STEP, none, h->nonunif, h->wall,
+                                     h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->cur ^= 1;
+    ++h->steps;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_moments(lbm_nphase_t *h, double *phi, double *c,
+                              double *u, double *p, double *rho) {
+  if (!h) return LBM_EINVAL;
+  if (!h->initialized) return LBM_ESTATE;
+  const size_t V = h->g.V;
+  const int N = h->prm.N;
+  double *ptr[5] = {phi, c, u, p, rho};
+  const int nf[5] = {N - 1, N, 2, 1, 1};
+  Outputs dev = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double **dslot[5] = {&dev.phi, &dev.c, &dev.u, &dev.p, &dev.rho};
+  bool any_dev = false, any_host = false;
+  for (int f = 0; f < 5; ++f) {
+    if (!ptr[f]) continue;
+    if (is_device_ptr(ptr[f])) {
+      *dslot[f] = ptr[f];
+      any_dev = true;
+    } else {
+      any_host = true;
+    }
+  }
+  cudaError_t e;
+  if (any_dev) {
+    e = lbm::launch_tile(h->prec, h->k, h->g, h->cur, lbm::MODE_MOMENTS, dev,
+                         h->nonunif, h->wall, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  if (any_host) {
+    for (int f = 0; f < 5; ++f) {
+      if (!ptr[f] || is_device_ptr(ptr[f])) continue;
+      Outputs one = {nullptr, nullptr, nullptr, nullptr, nullptr};
+      double **slot[5] = {&one.phi, &one.c, &one.u, &one.p, &one.rho};
+      *slot[f] = h->stage;
+      e = lbm::launch_tile(h->prec, h->k, h->g, h->cur, lbm::MODE_MOMENTS, one,
+                           h->nonunif, h->wall, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      e = cudaMemcpyAsync(ptr[f], h->stage, nf[f] * V * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+  }
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
+                                  double *umax) {
+  if (!h) return LBM_EINVAL;
+  if (!h->initialized) return LBM_ESTATE;
+  const int N = h->prm.N;
+  const Outputs none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = lbm::launch_tile(h->prec, h->k, h->g, h->cur, lbm::MODE_DIAG,
+                                   none, h->nonunif, h->wall, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  const int nparts = lbm::tiles_x(h->g.nx) * lbm::tiles_y(h->g.ny);
+  e = lbm::launch_reduce(h->g, nparts, N + 2, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  double r[LBM_MAX_N + 2];
+  e = cudaMemcpyAsync(r, h->g.red_out, (N + 2) * sizeof(double),
+                      cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  bool ok = true;
+  for (int j = 0; j < N + 2; ++j) ok = ok && isfinite(r[j]);
+  if (mass)
+    for (int k = 0; k < N; ++k) mass[k] = r[k];
+  if (ke) *ke = r[N];
+  if (umax) *umax = r[N + 1];
+  if (!ok) {
+    h->unstable = true;
+    return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h) { return h ? h->steps : 0; }
+
+int lbm_nphase_cuda_error(const lbm_nphase_t *h) { return h ? h->cuda_err : 0; }
+
+lbm_status lbm_nphase_destroy(lbm_nphase_t *h) {
+  delete h;
+  return LBM_OK;
+}
+
+}  // extern "C"

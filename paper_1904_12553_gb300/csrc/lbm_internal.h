@@ -1,0 +1,84 @@
+// Internal interface between the C-ABI host code and the per-precision CUDA
+// kernel translation units. Not part of the public API.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "lbm_nphase.h"
+
+namespace lbm {
+
+constexpr int BX = 32;  // tile width (one warp along x)
+constexpr int BY = 8;   // tile height
+constexpr int NT = BX * BY;
+
+enum Mode { MODE_STEP = 0, MODE_MOMENTS = 1, MODE_DIAG = 2 };
+
+// Model constants in FP64; each precision unit converts them to its type.
+// Index conventions: i, j over the N-1 order parameters; k over N phases.
+struct Consts {
+  int N, NP;
+  double lam[4][4];    // lambda_ij (Eq. N14)
+  double bulk;         // beta^2 / eta^2
+  double a[4];         // a_i (Eq. N30)
+  double tau_inv[4];   // 1 / tau_i
+  double src[4];       // 1 - 1/(2 tau_i) (Eq. N26)
+  double tg_inv;       // 1 / tau_g
+  double ffac;         // 1 - 1/(2 tau_g) (Eq. 24)
+  double jfac;         // 1 / (tau_g - 1/2) (Eq. N20_1)
+  double grav[2];      // G = rho * grav
+  double off[4], mul[4];  // varphi_j = off_j + mul_j phi_j (Eq. N12)
+  double c0[5];        // gamma~_k / Gamma (Eq. N18)
+  double Q[5][4];      // gamma~_k delta_kj - gamma~_k gamma~_j / Gamma
+  double rho_base;     // N / Gamma (Eq. N29)
+  double K[4];         // 1 - N gamma~_i / Gamma
+  double kap[4];       // K_i mul_i: grad rho = sum kap_i grad phi_i
+  double kmob[4];      // kap_i m_i: J~ = -sum kmob_i grad C_i
+  double rho_t[5];     // rho~_k (initialisation)
+  double sh, sg;       // 16-bit storage scales of h_k / w_k and g_k / w_k
+};
+
+// Device state of one grid. Buffers [0] and [1] alternate every step.
+struct Grid {
+  int nx, ny;
+  size_t V;
+  void *h0[2];      // rest populations h^i_0: [N-1][V] (FP64 or FP32)
+  void *hm[2];      // moving populations h^i_k, k = 1..8: [N-1][8][V]
+  void *gm[2];      // NS populations g_k, k = 1..8: [8][V]
+  void *phi_prev;   // phi_i(t-1): [N-1][V]
+  void *u_prev;     // u(t-1): [2][V]
+  double *red;      // per-block partial sums of the diagnostics
+  double *red_out;  // N + 2 reduced diagnostics
+};
+
+struct Outputs {
+  double *phi, *c, *u, *p, *rho;
+};
+
+// Launchers, one set per precision (lbm_fp64.cu, lbm_fp32.cu, lbm_mixed.cu).
+// prec is an lbm_precision value; `cur` selects the input buffer.
+cudaError_t launch_tile(int prec, const Consts &k, const Grid &g, int cur,
+                        int mode, const Outputs &o, bool nonunif, bool wall,
+                        cudaStream_t s);
+cudaError_t launch_init(int prec, const Consts &k, const Grid &g, int cur,
+                        const double *c, const double *u, double p0, bool wall,
+                        cudaStream_t s);
+cudaError_t launch_reduce(const Grid &g, int nparts, int nvals, cudaStream_t s);
+
+#define LBM_DECLARE_PREC(SUFFIX)                                              \
+  cudaError_t launch_tile_##SUFFIX(const Consts &, const Grid &, int, int,    \
+                                   const Outputs &, bool, bool, cudaStream_t);\
+  cudaError_t launch_init_##SUFFIX(const Consts &, const Grid &, int,         \
+                                   const double *, const double *, double,    \
+                                   bool, cudaStream_t);
+LBM_DECLARE_PREC(f64)
+LBM_DECLARE_PREC(f32)
+LBM_DECLARE_PREC(bf16)
+LBM_DECLARE_PREC(f16)
+#undef LBM_DECLARE_PREC
+
+inline int tiles_x(int nx) { return (nx + BX - 1) / BX; }
+inline int tiles_y(int ny) { return (ny + BY - 1) / BY; }
+
+}  // namespace lbm

@@ -1,0 +1,736 @@
+// Fused time-step kernels of the N-phase phase-field lattice Boltzmann model
+// (Yuan, Liang, Chai, Shi, arXiv:1904.12553) for sm_103a.
+//
+// Data layout (structure of arrays, x fastest, one plane per population):
+//   h0[i][V]        rest population h^i_0 of order parameter i
+//   hm[i][k-1][V]   moving populations h^i_k, k = 1..8
+//   gm[k-1][V]      NS populations g_k, k = 1..8 (g_0 never influences u, p
+//                   or phi: u has c_0 = 0 and Eq. N23 sums k >= 1)
+//   phi_prev[i][V], u_prev[2][V]   the t-1 state of Eq. N27
+// The stored populations are post-streaming values at their node (push
+// scheme), so phi_i(x) = sum_k h^i_k(x) is local (Eq. N28).
+//
+// One CTA owns a BX x BY tile. It sums the populations of the tile and of a
+// halo ring of radius R into shared memory (phi), evaluates the stencils of
+// Eq. N31 there, and for every own node computes C_i (Eqs. N17, N18),
+// F = sum C_i grad phi_i + rho G, u (Eq. N22_1), p (Eq. N23), the NS
+// collision (Eq. 24, Eq. 25, Eq. N20_1), the CH collisions (Eq. N24, Eq. N25,
+// Eqs. N26-N27), and pushes the post-collision populations to the
+// neighbours (periodic, or halfway bounce-back at y walls). With unequal
+// pure-phase densities, J~ needs grad C_i, so the CTA also evaluates C on a
+// ring of radius 1 and phi on a ring of radius 2 (R = 2).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// D2Q9 (Section 3.1): k = 0 rest; 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1);
+// 5 (1,1); 6 (-1,1); 7 (-1,-1); 8 (1,-1).
+__host__ __device__ constexpr int cx_of(int k) {
+  return (k == 1 || k == 5 || k == 8) ? 1 : ((k == 3 || k == 6 || k == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int k) {
+  return (k == 2 || k == 5 || k == 6) ? 1 : ((k == 4 || k == 7 || k == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_of(int k) {
+  return k == 0 ? 0 : (k <= 4 ? ((k + 1) % 4) + 1 : ((k - 5 + 2) % 4) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T w_of(int k) {
+  return k == 0 ? T(4) / T(9) : (k <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 &&
+                  opp_of(4) == 2 && opp_of(5) == 7 && opp_of(6) == 8 &&
+                  opp_of(7) == 5 && opp_of(8) == 6,
+              "opposite directions");
+
+// Storage policy per precision.
+template <int P> struct Prec;
+template <> struct Prec<LBM_FP64> {
+  typedef double T;
+  typedef double Sm;
+  static constexpr bool MIX = false;
+};
+template <> struct Prec<LBM_FP32> {
+  typedef float T;
+  typedef float Sm;
+  static constexpr bool MIX = false;
+};
+template <> struct Prec<LBM_MIX_BF16> {
+  typedef float T;
+  typedef __nv_bfloat16 Sm;
+  static constexpr bool MIX = true;
+};
+template <> struct Prec<LBM_MIX_FP16> {
+  typedef float T;
+  typedef __half Sm;
+  static constexpr bool MIX = true;
+};
+
+__device__ __forceinline__ float to_T(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_T(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_T(float v) { return v; }
+__device__ __forceinline__ double to_T(double v) { return v; }
+template <typename S> __device__ __forceinline__ S to_S(float v);
+template <> __device__ __forceinline__ __nv_bfloat16 to_S(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half to_S(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ float to_S(float v) { return v; }
+template <typename S> __device__ __forceinline__ S to_S(double v) { return v; }
+
+// Kernel arguments: pointers of one step and the model constants in T.
+template <int P> struct KArgs {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  int nx, ny;
+  size_t V;
+  const T *h0_in;
+  const Sm *hm_in, *gm_in;
+  T *h0_out;
+  Sm *hm_out, *gm_out;
+  T *phi_prev, *u_prev;
+  double *o_phi, *o_c, *o_u, *o_p, *o_rho, *red;
+  int mode;
+  T lam[4][4], bulk, a[4], tau_inv[4], src[4], tg_inv, ffac, jfac, grav[2];
+  T off[4], mul[4], c0[5], Q[5][4], rho_base, K[4], kap[4], kmob[4];
+  T sh_ld, sh_st, sg_ld, sg_st;  // 16-bit storage: value = S * w_k * ld
+};
+
+template <int P>
+KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
+                   const Outputs &o) {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  KArgs<P> a;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.V = g.V;
+  a.h0_in = (const T *)g.h0[cur];
+  a.hm_in = (const Sm *)g.hm[cur];
+  a.gm_in = (const Sm *)g.gm[cur];
+  a.h0_out = (T *)g.h0[cur ^ 1];
+  a.hm_out = (Sm *)g.hm[cur ^ 1];
+  a.gm_out = (Sm *)g.gm[cur ^ 1];
+  a.phi_prev = (T *)g.phi_prev;
+  a.u_prev = (T *)g.u_prev;
+  a.o_phi = o.phi;
+  a.o_c = o.c;
+  a.o_u = o.u;
+  a.o_p = o.p;
+  a.o_rho = o.rho;
+  a.red = g.red;
+  a.mode = mode;
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) a.lam[i][j] = (T)c.lam[i][j];
+    a.a[i] = (T)c.a[i];
+    a.tau_inv[i] = (T)c.tau_inv[i];
+    a.src[i] = (T)c.src[i];
+    a.off[i] = (T)c.off[i];
+    a.mul[i] = (T)c.mul[i];
+    a.K[i] = (T)c.K[i];
+    a.kap[i] = (T)c.kap[i];
+    a.kmob[i] = (T)c.kmob[i];
+  }
+  for (int k = 0; k < 5; ++k) {
+    a.c0[k] = (T)c.c0[k];
+    for (int j = 0; j < 4; ++j) a.Q[k][j] = (T)c.Q[k][j];
+  }
+  a.bulk = (T)c.bulk;
+  a.tg_inv = (T)c.tg_inv;
+  a.ffac = (T)c.ffac;
+  a.jfac = (T)c.jfac;
+  a.grav[0] = (T)c.grav[0];
+  a.grav[1] = (T)c.grav[1];
+  a.rho_base = (T)c.rho_base;
+  a.sh_ld = (T)(1.0 / c.sh);
+  a.sh_st = (T)c.sh;
+  a.sg_ld = (T)(1.0 / c.sg);
+  a.sg_st = (T)c.sg;
+  return a;
+}
+
+template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// Moving population k (1..8) of phase i at node q, in T.
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T load_hm(const KArgs<P> &a, int i,
+                                                       int k, size_t q) {
+  typedef typename Prec<P>::T T;
+  T v = to_T(ldg(a.hm_in + ((size_t)(i * 8 + k - 1)) * a.V + q));
+  if constexpr (Prec<P>::MIX) v *= w_of<T>(k) * a.sh_ld;
+  return v;
+}
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
+                                                       size_t q) {
+  typedef typename Prec<P>::T T;
+  T v = to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
+  if constexpr (Prec<P>::MIX) v *= w_of<T>(k) * a.sg_ld;
+  return v;
+}
+
+// Wrap an x coordinate periodically; y periodically or onto the wall rows
+// (ghost rows repeat the adjacent fluid row).
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+template <bool WALL>
+__device__ __forceinline__ int wrap_y(int v, int n) {
+  if (WALL) return v < 0 ? 0 : (v >= n ? n - 1 : v);
+  return wrap(v, n);
+}
+
+// Volume fractions (Eq. N18), density (Eq. N29) and h_i of Eq. N17 at one
+// node from its order parameters.
+template <int P, int NP>
+__device__ __forceinline__ void local_algebra(const KArgs<P> &a,
+                                              const typename Prec<P>::T *ph,
+                                              typename Prec<P>::T *c,
+                                              typename Prec<P>::T &rho,
+                                              typename Prec<P>::T *hf) {
+  typedef typename Prec<P>::T T;
+  T vp[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) vp[j] = a.off[j] + a.mul[j] * ph[j];
+  rho = a.rho_base;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) rho += a.K[j] * vp[j];
+  T f[NP + 1];
+#pragma unroll
+  for (int k = 0; k <= NP; ++k) {
+    T s = a.c0[k];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s += a.Q[k][j] * vp[j];
+    c[k] = s;
+    f[k] = s * (T(1) - s) * (T(1) - T(2) * s);
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k <= NP; ++k) s += a.Q[k][i] * f[k];
+    hf[i] = a.mul[i] * s;
+  }
+}
+
+// Isotropic central stencils of Eq. N31 on a shared-memory plane: the sums
+// over the 8 neighbours folded pairwise.
+template <typename T, int W>
+__device__ __forceinline__ void stencil(const T *s, int ly, int lx, T &gx,
+                                        T &gy, T &lap) {
+  const T c = s[ly * W + lx];
+  const T e = s[ly * W + lx + 1], w = s[ly * W + lx - 1];
+  const T n = s[(ly + 1) * W + lx], so = s[(ly - 1) * W + lx];
+  const T ne = s[(ly + 1) * W + lx + 1], nw = s[(ly + 1) * W + lx - 1];
+  const T se = s[(ly - 1) * W + lx + 1], sw = s[(ly - 1) * W + lx - 1];
+  gx = (e - w) * T(1.0 / 3.0) + ((ne + se) - (nw + sw)) * T(1.0 / 12.0);
+  gy = (n - so) * T(1.0 / 3.0) + ((ne + nw) - (se + sw)) * T(1.0 / 12.0);
+  lap = ((e + w) + (n + so) - T(4) * c) * T(2.0 / 3.0) +
+        ((ne + nw) + (se + sw) - T(4) * c) * T(1.0 / 6.0);
+}
+template <typename T, int W>
+__device__ __forceinline__ void gradient(const T *s, int ly, int lx, T &gx,
+                                         T &gy) {
+  const T e = s[ly * W + lx + 1], w = s[ly * W + lx - 1];
+  const T n = s[(ly + 1) * W + lx], so = s[(ly - 1) * W + lx];
+  const T ne = s[(ly + 1) * W + lx + 1], nw = s[(ly + 1) * W + lx - 1];
+  const T se = s[(ly - 1) * W + lx + 1], sw = s[(ly - 1) * W + lx - 1];
+  gx = (e - w) * T(1.0 / 3.0) + ((ne + se) - (nw + sw)) * T(1.0 / 12.0);
+  gy = (n - so) * T(1.0 / 3.0) + ((ne + nw) - (se + sw)) * T(1.0 / 12.0);
+}
+template <typename T, int W>
+__device__ __forceinline__ T laplacian(const T *s, int ly, int lx) {
+  const T c = s[ly * W + lx];
+  const T e = s[ly * W + lx + 1], w = s[ly * W + lx - 1];
+  const T n = s[(ly + 1) * W + lx], so = s[(ly - 1) * W + lx];
+  const T ne = s[(ly + 1) * W + lx + 1], nw = s[(ly + 1) * W + lx - 1];
+  const T se = s[(ly - 1) * W + lx + 1], sw = s[(ly - 1) * W + lx - 1];
+  return ((e + w) + (n + so) - T(4) * c) * T(2.0 / 3.0) +
+         ((ne + nw) + (se + sw) - T(4) * c) * T(1.0 / 6.0);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// The fused tile kernel (MODE_STEP: one time step; MODE_MOMENTS: write the
+// macroscopic fields; MODE_DIAG: per-CTA partial sums of the diagnostics).
+// ---------------------------------------------------------------------------
+template <int P, int NP, bool NU, bool WALL>
+__global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
+  typedef typename Prec<P>::T T;
+  constexpr int R = NU ? 2 : 1;     // phi halo radius
+  constexpr int SW = BX + 2 * R;    // shared tile width
+  constexpr int SH = BY + 2 * R;    // shared tile height
+  constexpr int CW = NU ? BX + 2 : 1, CH = NU ? BY + 2 : 1;
+  __shared__ T sphi[NP][SH * SW];
+  __shared__ T sC[NP][CH * CW];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int nx = a.nx, ny = a.ny;
+  const size_t V = a.V;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = gx < nx && gy < ny;
+
+  // 1. Own node: load all h^i_k, phi_i = sum_k h^i_k (Eq. N28).
+  T hreg[NP][9];
+  {
+    const int sx = wrap(gx, nx), sy = wrap_y<WALL>(gy, ny);
+    const size_t q = (size_t)sy * nx + sx;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      hreg[i][0] = ldg(a.h0_in + (size_t)i * V + q);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) hreg[i][k] = load_hm<P>(a, i, k, q);
+      T s = hreg[i][0];
+#pragma unroll
+      for (int k = 1; k < 9; ++k) s += hreg[i][k];
+      sphi[i][(ty + R) * SW + tx + R] = s;
+    }
+  }
+  // 2. Halo ring: top R rows, bottom R rows, left and right R columns.
+  constexpr int NRING = SW * SH - BX * BY;
+  for (int r = tid; r < NRING; r += NT) {
+    int lx, ly;
+    if (r < R * SW) {
+      ly = r / SW; lx = r % SW;
+    } else if (r < 2 * R * SW) {
+      int t = r - R * SW; ly = R + BY + t / SW; lx = t % SW;
+    } else if (r < 2 * R * SW + R * BY) {
+      int t = r - 2 * R * SW; ly = R + t / R; lx = t % R;
+    } else {
+      int t = r - 2 * R * SW - R * BY; ly = R + t / R; lx = R + BX + t % R;
+    }
+    const int sx = wrap(x0 - R + lx, nx), sy = wrap_y<WALL>(y0 - R + ly, ny);
+    const size_t q = (size_t)sy * nx + sx;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T s = ldg(a.h0_in + (size_t)i * V + q);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) s += load_hm<P>(a, i, k, q);
+      sphi[i][ly * SW + lx] = s;
+    }
+  }
+  __syncthreads();
+
+  // 3. Unequal densities: C_i on the tile and a ring of radius 1, then wall
+  //    ghost rows of C repeat the adjacent fluid row.
+  if constexpr (NU) {
+    for (int r = tid; r < CW * CH; r += NT) {
+      const int cy = r / CW, cxl = r % CW;
+      T ph[NP], lp[NP], cc[NP + 1], rho, hf[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        ph[i] = sphi[i][(cy + 1) * SW + cxl + 1];
+        lp[i] = laplacian<T, SW>(sphi[i], cy + 1, cxl + 1);
+      }
+      local_algebra<P, NP>(a, ph, cc, rho, hf);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T Ci = a.bulk * hf[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+        sC[i][r] = Ci;
+      }
+    }
+    __syncthreads();
+    if constexpr (WALL) {
+      for (int r = tid; r < CW * CH; r += NT) {
+        const int cy = r / CW, cxl = r % CW;
+        const int yg = y0 - 1 + cy;
+        if (yg < 0 || yg >= ny) {
+          const int ys = yg < 0 ? 0 : ny - 1;
+          const int cys = ys - y0 + 1;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) sC[i][r] = sC[i][cys * CW + cxl];
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // 4. Own node: stencils, C_i, forces, u, p.
+  const int ly = ty + R, lx = tx + R;
+  T ph[NP], gpx[NP], gpy[NP], Cv[NP];
+  T cc[NP + 1], rho;
+  {
+    T lp[NP], hf[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      ph[i] = sphi[i][ly * SW + lx];
+      stencil<T, SW>(sphi[i], ly, lx, gpx[i], gpy[i], lp[i]);
+    }
+    local_algebra<P, NP>(a, ph, cc, rho, hf);
+    if constexpr (NU) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) Cv[i] = sC[i][(ty + 1) * CW + tx + 1];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T Ci = a.bulk * hf[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+        Cv[i] = Ci;
+      }
+    }
+  }
+  T grx = T(0), gry = T(0), Jx = T(0), Jy = T(0);
+  if constexpr (NU) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T cgx, cgy;
+      gradient<T, CW>(sC[i], ty + 1, tx + 1, cgx, cgy);
+      Jx -= a.kmob[i] * cgx;
+      Jy -= a.kmob[i] * cgy;
+      grx += a.kap[i] * gpx[i];
+      gry += a.kap[i] * gpy[i];
+    }
+  }
+  T Fx = rho * a.grav[0], Fy = rho * a.grav[1];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    Fx += Cv[i] * gpx[i];
+    Fy += Cv[i] * gpy[i];
+  }
+  const size_t q = (size_t)(active ? gy : 0) * nx + (active ? gx : 0);
+  T g[9];
+  T mx = T(0), my = T(0), sg = T(0);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    g[k] = active ? load_gm<P>(a, k, q) : T(0);
+    mx += T(cx_of(k)) * g[k];
+    my += T(cy_of(k)) * g[k];
+    sg += g[k];
+  }
+  const T rinv = T(1) / rho;
+  const T ux = (mx + T(0.5) * Fx) * rinv, uy = (my + T(0.5) * Fy) * rinv;
+  const T uu = ux * ux + uy * uy;
+  const T ugr = ux * grx + uy * gry;
+  // Eq. N23: c_s^2/(1-w_0) = 3/5; s_0(u) = -w_0 |u|^2 / (2 c_s^2)
+  const T pr = T(0.6) * (sg + T(0.5) * ugr - rho * T(4.0 / 9.0) * T(1.5) * uu);
+
+  if (a.mode == MODE_MOMENTS) {
+    if (!active) return;
+    if (a.o_phi)
+#pragma unroll
+      for (int i = 0; i < NP; ++i) a.o_phi[(size_t)i * V + q] = (double)ph[i];
+    if (a.o_c)
+#pragma unroll
+      for (int k = 0; k <= NP; ++k) a.o_c[(size_t)k * V + q] = (double)cc[k];
+    if (a.o_u) {
+      a.o_u[q] = (double)ux;
+      a.o_u[V + q] = (double)uy;
+    }
+    if (a.o_p) a.o_p[q] = (double)pr;
+    if (a.o_rho) a.o_rho[q] = (double)rho;
+    return;
+  }
+  if (a.mode == MODE_DIAG) {
+    // mass_k, ke, umax: warp shuffle, then warps in fixed order.
+    __shared__ double sred[NT / 32][NP + 3];
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k <= NP + 2; ++k) {
+      double v;
+      if (k <= NP) v = active ? (double)cc[k] : 0.0;
+      else if (k == NP + 1) v = active ? 0.5 * (double)rho * (double)uu : 0.0;
+      else v = active ? sqrt((double)uu) : 0.0;
+      v = (k == NP + 2) ? warp_max(v) : warp_sum(v);
+      if (lane == 0) sred[wid][k] = v;
+    }
+    __syncthreads();
+    if (tid <= NP + 2) {
+      double v = sred[0][tid];
+      for (int w = 1; w < NT / 32; ++w)
+        v = (tid == NP + 2) ? fmax(v, sred[w][tid]) : v + sred[w][tid];
+      a.red[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (NP + 3) + tid] = v;
+    }
+    return;
+  }
+  if (!active) return;
+
+  // 5. NS collision (Eq. 24) with g^eq (Eq. 25) and G_k (Eq. N20_1), then
+  //    push to x + c_k.
+  const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+  const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
+  const T uF = ux * Fx + uy * Fy;
+  const T Ju = (Jx * ux + Jy * uy) * a.jfac;
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
+    const T wk = w_of<T>(k);
+    const T cu = cxk * ux + cyk * uy;
+    const T cF = cxk * Fx + cyk * Fy;
+    const T geq = wk * (T(3) * pr + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    // (c c - c_s^2 I) : T / (2 c_s^4) with T = uF + Fu + c_s^2 (u grad rho +
+    // grad rho u) + J~u / (tau_g - 1/2)
+    T QT = T(2) * cu * cF - T(2.0 / 3.0) * uF;
+    if constexpr (NU) {
+      const T cr = cxk * grx + cyk * gry;
+      const T cJ = cxk * Jx + cyk * Jy;
+      QT += T(2.0 / 3.0) * cu * cr - T(2.0 / 9.0) * ugr + cJ * cu * a.jfac -
+            T(1.0 / 3.0) * Ju;
+    }
+    const T Gk = wk * (ugr + T(3) * cF + T(4.5) * QT);
+    const T gs = g[k] - (g[k] - geq) * a.tg_inv + a.ffac * Gk;
+    // destination
+    const int cxi = cx_of(k), cyi = cy_of(k);
+    const int dx = cxi == 0 ? gx : (cxi > 0 ? xp : xm);
+    int dy = cyi == 0 ? gy : (cyi > 0 ? yp : ym);
+    int kk = k;
+    int ddx = dx;
+    if (WALL && ((cyi < 0 && gy == 0) || (cyi > 0 && gy == ny - 1))) {
+      dy = gy;
+      ddx = gx;
+      kk = opp_of(k);
+    }
+    const size_t d = (size_t)dy * nx + ddx;
+    if constexpr (Prec<P>::MIX)
+      a.gm_out[(size_t)(kk - 1) * V + d] = to_S<typename Prec<P>::Sm>(gs * (a.sg_st / w_of<T>(kk)));
+    else
+      a.gm_out[(size_t)(kk - 1) * V + d] = gs;
+  }
+
+  // 6. CH collisions (Eq. N24) with h^eq (Eq. N25) and R_k (Eqs. N26, N27).
+  const T upx = a.u_prev[q], upy = a.u_prev[V + q];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const T pp = a.phi_prev[(size_t)i * V + q];
+    const T dpx = ph[i] * ux - pp * upx, dpy = ph[i] * uy - pp * upy;
+    const T aC = a.a[i] * Cv[i];
+    const T ti = a.tau_inv[i];
+    const T sr = a.src[i] * T(3);
+    T moving_sum = T(0);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+      const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
+      const T wk = w_of<T>(k);
+      const T heq = wk * (aC + T(3) * ph[i] * (cxk * ux + cyk * uy));
+      const T Rk = sr * wk * (cxk * dpx + cyk * dpy);
+      T hs = hreg[i][k] - (hreg[i][k] - heq) * ti + Rk;
+      const int cxi = cx_of(k), cyi = cy_of(k);
+      const int dx = cxi == 0 ? gx : (cxi > 0 ? xp : xm);
+      int dy = cyi == 0 ? gy : (cyi > 0 ? yp : ym);
+      int kk = k;
+      int ddx = dx;
+      if (WALL && ((cyi < 0 && gy == 0) || (cyi > 0 && gy == ny - 1))) {
+        dy = gy;
+        ddx = gx;
+        kk = opp_of(k);
+      }
+      const size_t d = (size_t)dy * nx + ddx;
+      if constexpr (Prec<P>::MIX) {
+        // 16-bit storage of h_k / w_k; the rest slot below absorbs the
+        // rounding so that sum_k h*_k = phi_i exactly as in the collision.
+        const auto sv = to_S<typename Prec<P>::Sm>(hs * (a.sh_st / w_of<T>(kk)));
+        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + d] = sv;
+        moving_sum += to_T(sv) * (w_of<T>(kk) * a.sh_ld);
+      } else {
+        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + d] = hs;
+      }
+    }
+    T h0s;
+    if constexpr (Prec<P>::MIX) {
+      h0s = ph[i] - moving_sum;
+    } else {
+      const T heq0 = ph[i] + (w_of<T>(0) - T(1)) * aC;
+      h0s = hreg[i][0] - (hreg[i][0] - heq0) * ti;
+    }
+    a.h0_out[(size_t)i * V + q] = h0s;
+    a.phi_prev[(size_t)i * V + q] = ph[i];
+  }
+  a.u_prev[q] = ux;
+  a.u_prev[V + q] = uy;
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation: phi from c (inverse of Eqs. N2, N12), then h = h^eq and
+// g = g^eq at the stencil C_i.
+// ---------------------------------------------------------------------------
+template <int P, int NP>
+__global__ void init_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
+                                const double *__restrict__ u, double r0,
+                                double r1, double r2, double r3, double r4) {
+  typedef typename Prec<P>::T T;
+  const double rt[5] = {r0, r1, r2, r3, r4};
+  const double rN = rt[NP];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < a.V;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const double cN = c[(size_t)NP * a.V + q];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const double ci = c[(size_t)i * a.V + q];
+      const double ph = (2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN);
+      a.phi_prev[(size_t)i * a.V + q] = (T)ph;
+    }
+    a.u_prev[q] = u ? (T)u[q] : T(0);
+    a.u_prev[a.V + q] = u ? (T)u[a.V + q] : T(0);
+  }
+}
+
+template <int P, int NP, bool WALL>
+__global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  const int nx = a.nx, ny = a.ny;
+  const size_t V = a.V;
+  T *h0 = a.h0_out;
+  Sm *hm = a.hm_out;
+  Sm *gm = a.gm_out;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < V;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(q % nx), y = (int)(q / nx);
+    T ph[NP], lp[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const T *f = a.phi_prev + (size_t)i * V;
+      T s[9];
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx)
+          s[(dy + 1) * 3 + dx + 1] =
+              f[(size_t)wrap_y<WALL>(y + dy, ny) * nx + wrap(x + dx, nx)];
+      ph[i] = s[4];
+      lp[i] = laplacian<T, 3>(s, 1, 1);
+    }
+    T cc[NP + 1], rho, hf[NP];
+    local_algebra<P, NP>(a, ph, cc, rho, hf);
+    const T ux = a.u_prev[q], uy = a.u_prev[V + q];
+    const T uu = ux * ux + uy * uy;
+    const T p0 = (T)p0d;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+      const T cu = T(cx_of(k)) * ux + T(cy_of(k)) * uy;
+      const T geq = w_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+      if constexpr (Prec<P>::MIX)
+        gm[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w_of<T>(k)));
+      else
+        gm[(size_t)(k - 1) * V + q] = geq;
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T Ci = a.bulk * hf[i];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+      const T aC = a.a[i] * Ci;
+      T moving = T(0);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) {
+        const T heq = w_of<T>(k) * (aC + T(3) * ph[i] * (T(cx_of(k)) * ux + T(cy_of(k)) * uy));
+        if constexpr (Prec<P>::MIX) {
+          const Sm sv = to_S<Sm>(heq * (a.sh_st / w_of<T>(k)));
+          hm[((size_t)(i * 8 + k - 1)) * V + q] = sv;
+          moving += to_T(sv) * (w_of<T>(k) * a.sh_ld);
+        } else {
+          hm[((size_t)(i * 8 + k - 1)) * V + q] = heq;
+        }
+      }
+      if constexpr (Prec<P>::MIX)
+        h0[(size_t)i * V + q] = ph[i] - moving;
+      else
+        h0[(size_t)i * V + q] = ph[i] + (w_of<T>(0) - T(1)) * aC;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers for one precision.
+// ---------------------------------------------------------------------------
+template <int P, int NP, bool NU, bool WALL>
+cudaError_t launch_tile_t(const Consts &c, const Grid &g, int cur, int mode,
+                          const Outputs &o, cudaStream_t s) {
+  const KArgs<P> a = make_args<P>(c, g, cur, mode, o);
+  dim3 grid(tiles_x(g.nx), tiles_y(g.ny)), block(BX, BY);
+  tile_kernel<P, NP, NU, WALL><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int NP>
+cudaError_t launch_tile_np(const Consts &c, const Grid &g, int cur, int mode,
+                           const Outputs &o, bool nonunif, bool wall,
+                           cudaStream_t s) {
+  if (nonunif)
+    return wall ? launch_tile_t<P, NP, true, true>(c, g, cur, mode, o, s)
+                : launch_tile_t<P, NP, true, false>(c, g, cur, mode, o, s);
+  return wall ? launch_tile_t<P, NP, false, true>(c, g, cur, mode, o, s)
+              : launch_tile_t<P, NP, false, false>(c, g, cur, mode, o, s);
+}
+
+template <int P>
+cudaError_t launch_tile_p(const Consts &c, const Grid &g, int cur, int mode,
+                          const Outputs &o, bool nonunif, bool wall,
+                          cudaStream_t s) {
+  switch (c.NP) {
+    case 1: return launch_tile_np<P, 1>(c, g, cur, mode, o, nonunif, wall, s);
+    case 2: return launch_tile_np<P, 2>(c, g, cur, mode, o, nonunif, wall, s);
+    case 3: return launch_tile_np<P, 3>(c, g, cur, mode, o, nonunif, wall, s);
+    case 4: return launch_tile_np<P, 4>(c, g, cur, mode, o, nonunif, wall, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int NP>
+cudaError_t launch_init_np(const Consts &c, const Grid &g, int cur,
+                           const double *cin, const double *uin, double p0,
+                           bool wall, cudaStream_t s) {
+  // The init kernels write into buffer `cur`: make_args puts the output
+  // pointers at cur ^ 1, so pass cur ^ 1.
+  const KArgs<P> a = make_args<P>(c, g, cur ^ 1, MODE_STEP, Outputs{});
+  const int threads = 256;
+  size_t blocks = (g.V + threads - 1) / threads;
+  if (blocks > 65535u * 16u) blocks = 65535u * 16u;
+  init_phi_kernel<P, NP><<<(unsigned)blocks, threads, 0, s>>>(
+      a, cin, uin, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (wall)
+    init_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(a, p0);
+  else
+    init_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(a, p0);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_init_p(const Consts &c, const Grid &g, int cur,
+                          const double *cin, const double *uin, double p0,
+                          bool wall, cudaStream_t s) {
+  switch (c.NP) {
+    case 1: return launch_init_np<P, 1>(c, g, cur, cin, uin, p0, wall, s);
+    case 2: return launch_init_np<P, 2>(c, g, cur, cin, uin, p0, wall, s);
+    case 3: return launch_init_np<P, 3>(c, g, cur, cin, uin, p0, wall, s);
+    case 4: return launch_init_np<P, 4>(c, g, cur, cin, uin, p0, wall, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm
+
+#define LBM_DEFINE_PREC(SUFFIX, P)                                             \
+  namespace lbm {                                                              \
+  cudaError_t launch_tile_##SUFFIX(const Consts &c, const Grid &g, int cur,    \
+                                   int mode, const Outputs &o, bool nonunif,   \
+                                   bool wall, cudaStream_t s) {                \
+    return launch_tile_p<P>(c, g, cur, mode, o, nonunif, wall, s);             \
+  }                                                                            \
+  cudaError_t launch_init_##SUFFIX(const Consts &c, const Grid &g, int cur,    \
+                                   const double *cin, const double *uin,       \
+                                   double p0, bool wall, cudaStream_t s) {     \
+    return launch_init_p<P>(c, g, cur, cin, uin, p0, wall, s);                 \
+  }                                                                            \
+  }

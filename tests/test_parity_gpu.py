@@ -1,0 +1,260 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 after 1000 steps max|dphi| <= 1e-10, max|du| <= 1e-12 (the
+accuracy target of the solver); short FP64 runs at roundoff level; FP32 and
+16-bit storage forms max|dphi| <= 1e-3 against the FP64 oracle, relative
+mass drift <= 1e-6.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_12553_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_12553_gb300 import build
+    build.build()
+
+
+def _accept(N=None, rho=None):
+    """sigma draws with a well-conditioned lambda (oracle's Eq. N14)."""
+    def ok(sig):
+        p = W.base_params(sig.shape[0], 4, 4, sig, rho=rho)
+        ev = np.linalg.eigvalsh(oracle.lam(p))
+        return ev[0] > 1e-3 * ev[-1]
+    return ok
+
+
+def gpu_run(w, steps, prec=None, **kw):
+    from paper_1904_12553_gb300 import Solver
+    p = dict(w.params)
+    if prec:
+        p["precision"] = prec
+    s = Solver(p)
+    s.init(w.c0, w.u0, w.p0)
+    s.step(steps)
+    m = s.moments()
+    d = s.diagnostics() if kw.get("diag") else None
+    s.close()
+    return (m, d) if kw.get("diag") else m
+
+
+def oracle_run(w, steps, diag=False):
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0, w.u0, w.p0)
+    s.step(steps)
+    m = s.moments()
+    d = s.diagnostics() if diag else None
+    s.close()
+    return (m, d) if diag else m
+
+
+def maxdiff(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max())
+
+
+def compare(g, o, tol_phi, tol_u, tol_p=None):
+    dphi, du = maxdiff(g["phi"], o["phi"]), maxdiff(g["u"], o["u"])
+    assert dphi <= tol_phi, ("phi", dphi)
+    assert du <= tol_u, ("u", du)
+    if tol_p is not None:
+        assert maxdiff(g["p"], o["p"]) <= tol_p, ("p", maxdiff(g["p"], o["p"]))
+    assert maxdiff(g["c"], o["c"]) <= 2 * tol_phi * 20
+    assert maxdiff(g["rho"], o["rho"]) <= 40 * tol_phi
+
+
+# ---------------------------------------------------------------------------
+# FP64 brute force on small grids: every N, walls, unequal densities, tiles
+# with ragged tails and grids smaller than one tile.
+# ---------------------------------------------------------------------------
+
+CASES = [(N, nx, ny, wall, nonunif)
+         for N in (2, 3, 4, 5)
+         for (nx, ny) in ((8, 8), (37, 29), (5, 3), (70, 45))
+         for wall in (0, 1)
+         for nonunif in (False, True)]
+
+
+@pytest.mark.parametrize("N,nx,ny,wall,nonunif", CASES)
+def test_fp64_short_runs(N, nx, ny, wall, nonunif):
+    seed = 1000 * N + 10 * nx + ny + 7 * wall + int(nonunif)
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.5, 8.0, N) if nonunif else None
+    w = W.random_smooth(seed, N, nx, ny, rho=rho, wall_y=wall, amp_u=0.02,
+                        gravity=(1e-5, -2e-5) if nonunif else (0.0, 0.0),
+                        sigma=W.sample_sigma(rng, N, accept=_accept(N, rho)))
+    for steps in (1, 20):
+        g = gpu_run(w, steps)
+        o = oracle_run(w, steps)
+        compare(g, o, 1e-12, 1e-13, 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# The accuracy target: FP64, 1000 steps.
+# ---------------------------------------------------------------------------
+
+def test_static_drops_fp64_1000_steps():
+    """N=3 static drops, 128x128 periodic (R=20 at (40,64) and (88,64),
+    sigma=1e-3, tau=0.8, M=0.1)."""
+    w = W.static_drops()
+    g, gd = gpu_run(w, 1000, diag=True)
+    o, od = oracle_run(w, 1000, diag=True)
+    compare(g, o, 1e-10, 1e-12)
+    np.testing.assert_allclose(gd[0], od[0], rtol=1e-12)
+    assert abs(gd[1] - od[1]) <= 1e-9 * od[1] + 1e-20
+    assert abs(gd[2] - od[2]) <= 1e-12
+
+
+def test_lens_walls_fp64_1000_steps():
+    """Liquid lens geometry with bounce-back walls, reduced to 96x96."""
+    w = W.lens(nx=96, ny=96, R=16, s13=0.6e-3, precision="fp64")
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
+def test_collision_n4_fp64_1000_steps():
+    """N=4 drop collision with initial velocities, seeded sigma and tau,
+    reduced to 128x128."""
+    w = W.collision(seed=3, n=128, precision="fp64", accept=_accept(4))
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
+def test_droplets_interfaces_n5_fp64_1000_steps():
+    """N=5 layers plus drops, seeded, reduced to 128x128."""
+    w = W.droplets_interfaces(seed=4, n=128, ndrops=6, precision="fp64",
+                              accept=_accept(5))
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
+def test_unequal_density_fp64_1000_steps():
+    """Four phases with densities 20:1:10:5 (Section 4.1): J~ and grad rho
+    terms active."""
+    w = W.static_drops(nx=96, ny=64, R=12, N=4,
+                       centres=((20, 32), (48, 32), (76, 32)),
+                       rho=[20.0, 1.0, 10.0, 5.0], sigma=1e-3,
+                       mobility=0.01)
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
+def test_ensemble_cases_fp64():
+    """The first cases of the batched ensemble (sides 64 and 96), one by one."""
+    import paper_1904_12553_gb300 as P
+    for w in W.ensemble(seed=5, ncases=6, sides=(64, 96), accept=_accept()):
+        w.params["precision"] = "fp64"
+        P.lbm_nphase_derive(w.params)
+        compare(gpu_run(w, 200), oracle_run(w, 200), 1e-10, 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision storage forms against the FP64 oracle.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_precision_forms_error(prec):
+    w = W.static_drops()
+    o, od = oracle_run(w, 1000, diag=True)
+    g, gd = gpu_run(w, 1000, prec=prec, diag=True)
+    dphi = maxdiff(g["phi"], o["phi"])
+    assert dphi <= 1e-3, dphi
+    assert np.abs(gd[0] / od[0] - 1).max() <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_precision_forms_mass_drift_1e4_steps(prec):
+    w = W.static_drops()
+    from paper_1904_12553_gb300 import Solver
+    s = Solver({**w.params, "precision": prec})
+    s.init(w.c0)
+    m0, _, _ = s.diagnostics()
+    s.step(10000)
+    m1, ke, _ = s.diagnostics()
+    s.close()
+    assert np.abs(m1 / m0 - 1).max() <= 1e-6, (m0, m1)
+    assert math.isfinite(ke)
+
+
+# ---------------------------------------------------------------------------
+# Full size of the N=5 2048x2048 workload, in the benchmarked form (FP32).
+# ---------------------------------------------------------------------------
+
+def test_full_size_n5_2048_fp32():
+    w = W.droplets_interfaces(seed=4, n=2048, precision="fp32",
+                              accept=_accept(5))
+    g = gpu_run(w, 2)
+    o = oracle_run(w, 2)
+    assert maxdiff(g["phi"], o["phi"]) <= 2e-6
+    assert maxdiff(g["u"], o["u"]) <= 1e-9
+    np.testing.assert_allclose(g["c"].sum(0), 1.0, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Properties and API behaviour
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("wall", [0, 1])
+def test_quiescent_exact(prec, wall):
+    w = W.quiescent(4, 40, 19, frac=[0.1, 0.2, 0.3, 0.4], rho=[2, 1, 3, 7],
+                    precision=prec, wall_y=wall)
+    g = gpu_run(w, 500)
+    assert np.abs(g["u"]).max() == 0.0
+    assert np.ptp(g["phi"], axis=(1, 2)).max() == 0.0
+
+
+def test_deterministic():
+    w = W.random_smooth(11, 4, 67, 33, rho=[1, 2, 3, 4], amp_u=0.01)
+    a = gpu_run(w, 50)
+    b = gpu_run(w, 50)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+
+
+def test_host_and_device_pointers_agree():
+    from paper_1904_12553_gb300 import Solver, lbm_nphase_moments
+    w = W.random_smooth(12, 3, 33, 20, amp_u=0.01)
+    s1 = Solver(w.params)
+    s1.init(w.c0, w.u0)                                   # host numpy
+    s2 = Solver(w.params)
+    s2.init(torch.from_numpy(w.c0).cuda(), torch.from_numpy(w.u0).cuda())
+    s1.step(10)
+    s2.step(10)
+    a, b = s1.moments(), s2.moments()
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+    host = np.zeros((2, 20, 33))
+    lbm_nphase_moments(s1.handle, u=host.ctypes.data)
+    assert np.array_equal(host, a["u"])
+
+
+def test_state_errors():
+    from paper_1904_12553_gb300 import LbmError, Solver
+    w = W.random_smooth(13, 3, 16, 16, amp_u=0.01)
+    s = Solver(w.params)
+    with pytest.raises(LbmError) as e:
+        s.step(1)
+    assert e.value.status == 6                     # LBM_ESTATE before init
+    u = w.u0.copy()
+    u[0, 3, 4] = np.nan                             # made on the host
+    s.init(w.c0, u)
+    s.step(3)
+    with pytest.raises(LbmError) as e:
+        s.diagnostics()
+    assert e.value.status == 5                     # LBM_EUNSTABLE
+    with pytest.raises(LbmError) as e:
+        s.step(1)
+    assert e.value.status == 6
+    s.init(w.c0, w.u0)                              # re-init clears it
+    s.step(3)
+    mass, ke, um = s.diagnostics()
+    assert np.isfinite(mass).all() and math.isfinite(ke)
+    s.close()
