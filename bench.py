@@ -262,7 +262,7 @@ def run_ours(args, dist, rank, world):
         build.build()
     if dist:
         dist.barrier()
-    w = make_workload("fp32", accept=accept_sigma(5))
+    w = make_workload("fp32", n=args.n, accept=accept_sigma(5))
     N, V = w.params["N"], w.V
     sampler = ClockSampler(local) if rank == 0 else None
     ms, (wa, wb), mass, ke = time_form(w, "fp32", args.steps, args.warmup,
@@ -277,6 +277,14 @@ def run_ours(args, dist, rank, world):
     peak, peak_kind = peaks()
     B = alg_bytes_per_node(N, "fp32")
     achieved = B * V / (ms_step / 1e3) / 1e9
+    if args.kernel_only:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS",
+                          "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms_step,
+                          "kernel_only": True, "nx": w.params["nx"],
+                          "hbm_frac": B * V / (ms_step / 1e3) / 1e9 / peak,
+                          "clocks": clocks}), flush=True)
+        return
     forms = {}
     if not args.quick:
         for prec, k in (("bf16", args.steps), ("fp16", args.steps),
@@ -384,6 +392,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="skip the other storage forms and the CPU baseline")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time the FP32 step kernel only (profiling runs)")
+    ap.add_argument("--n", type=int, default=2048,
+                    help="grid side (2048 is the benchmark workload; smaller "
+                         "sides are for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -184,7 +184,7 @@ Layout layout(const lbm_nphase_params *p) {
   L.h0 = off;       off += 2 * align256(NP * V * sT);
   L.hm = off;       off += 2 * align256(NP * 8 * V * sS);
   L.gm = off;       off += 2 * align256(8 * V * sS);
-  L.phi_prev = off; off += align256(NP * V * sT);
+  L.phi_prev = off; off += 2 * align256(NP * V * sT);
   L.u_prev = off;   off += align256(2 * V * sT);
   L.stage = off;    off += align256((p->N + 2) * V * 8);
   L.red = off;      off += align256(tiles * (p->N + 2) * 8);
@@ -415,7 +415,9 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
     g.hm[b] = base + L.hm + b * hmb;
     g.gm[b] = base + L.gm + b * gmb;
   }
-  g.phi_prev = base + L.phi_prev;
+  const size_t ppb = align256(n * g.V * sT);
+  g.phi_prev[0] = base + L.phi_prev;
+  g.phi_prev[1] = base + L.phi_prev + ppb;
   g.u_prev = base + L.u_prev;
   h->stage = (double *)(base + L.stage);
   g.red = (double *)(base + L.red);

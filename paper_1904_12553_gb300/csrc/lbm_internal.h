@@ -43,10 +43,10 @@ struct Consts {
 struct Grid {
   int nx, ny;
   size_t V;
-  void *h0[2];      // rest populations h^i_0: [N-1][V] (FP64 or FP32)
+  void *h0[2];      // rest slots: h^i_0 (FP64) or h^i_0 - phi_i(t-1): [N-1][V]
   void *hm[2];      // moving populations h^i_k, k = 1..8: [N-1][8][V]
   void *gm[2];      // NS populations g_k, k = 1..8: [8][V]
-  void *phi_prev;   // phi_i(t-1): [N-1][V]
+  void *phi_prev[2];  // phi_i(t-1): [N-1][V]
   void *u_prev;     // u(t-1): [2][V]
   double *red;      // per-block partial sums of the diagnostics
   double *red_out;  // N + 2 reduced diagnostics

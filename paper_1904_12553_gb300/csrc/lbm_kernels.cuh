@@ -6,9 +6,16 @@
 //   hm[i][k-1][V]   moving populations h^i_k, k = 1..8
 //   gm[k-1][V]      NS populations g_k, k = 1..8 (g_0 never influences u, p
 //                   or phi: u has c_0 = 0 and Eq. N23 sums k >= 1)
-//   phi_prev[i][V], u_prev[2][V]   the t-1 state of Eq. N27
+//   phi_prev[2][i][V]   phi_i(t-1) (Eq. N27), ping-pong; u_prev[2][V] in place
 // The stored populations are post-streaming values at their node (push
 // scheme), so phi_i(x) = sum_k h^i_k(x) is local (Eq. N28).
+//
+// FP64 stores the rest population h^i_0 itself. The FP32 and 16-bit forms
+// store d^i_0 = h^i_0 - phi_i(t-1) instead, a value of the size of the moving
+// populations, and carry in it the exact rounding error of phi_i: the node's
+// mass phi_prev + d_0 + sum_k h_k is then conserved by the collision up to
+// the rounding of d_0 (~1e-11), where an O(1) FP32 rest slot would lose
+// ~6e-8 per node and step, systematically in a near-steady state.
 //
 // One CTA owns a BX x BY tile. It sums the populations of the tile and of a
 // halo ring of radius R into shared memory (phi), evaluates the stencils of
@@ -73,6 +80,8 @@ template <> struct Prec<LBM_MIX_FP16> {
   static constexpr bool MIX = true;
 };
 
+__device__ __forceinline__ float __fadd_rn_T(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double __fadd_rn_T(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float to_T(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_T(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_T(float v) { return v; }
@@ -93,7 +102,9 @@ template <int P> struct KArgs {
   const Sm *hm_in, *gm_in;
   T *h0_out;
   Sm *hm_out, *gm_out;
-  T *phi_prev, *u_prev;
+  const T *pp_in;  // phi_prev at t-1
+  T *pp_out;       // phi_prev for the next step (phi at t)
+  T *u_prev;
   double *o_phi, *o_c, *o_u, *o_p, *o_rho, *red;
   int mode;
   T lam[4][4], bulk, a[4], tau_inv[4], src[4], tg_inv, ffac, jfac, grav[2];
@@ -116,7 +127,8 @@ KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
   a.h0_out = (T *)g.h0[cur ^ 1];
   a.hm_out = (Sm *)g.hm[cur ^ 1];
   a.gm_out = (Sm *)g.gm[cur ^ 1];
-  a.phi_prev = (T *)g.phi_prev;
+  a.pp_in = (const T *)g.phi_prev[cur];
+  a.pp_out = (T *)g.phi_prev[cur ^ 1];
   a.u_prev = (T *)g.u_prev;
   a.o_phi = o.phi;
   a.o_c = o.c;
@@ -162,7 +174,7 @@ __device__ __forceinline__ typename Prec<P>::T load_hm(const KArgs<P> &a, int i,
                                                        int k, size_t q) {
   typedef typename Prec<P>::T T;
   T v = to_T(ldg(a.hm_in + ((size_t)(i * 8 + k - 1)) * a.V + q));
-  if constexpr (Prec<P>::MIX) v *= w_of<T>(k) * a.sh_ld;
+  if constexpr (Prec<P>::MIX) v = __fmul_rn(v, w_of<T>(k) * a.sh_ld);
   return v;
 }
 template <int P>
@@ -170,8 +182,30 @@ __device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
                                                        size_t q) {
   typedef typename Prec<P>::T T;
   T v = to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
-  if constexpr (Prec<P>::MIX) v *= w_of<T>(k) * a.sg_ld;
+  if constexpr (Prec<P>::MIX) v = __fmul_rn(v, w_of<T>(k) * a.sg_ld);
   return v;
+}
+
+// Order parameter of one node from its stored values. FP64: sum of the nine
+// populations. Other forms: phi_prev + (d_0 + sum_{k>=1} h_k), with the exact
+// rounding error of that last addition returned in err (TwoSum).
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T node_phi(
+    typename Prec<P>::T rest, const typename Prec<P>::T *mov,
+    typename Prec<P>::T pp, typename Prec<P>::T &err) {
+  typedef typename Prec<P>::T T;
+  T small = rest;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) small = __fadd_rn_T(small, mov[k]);
+  if constexpr (P == LBM_FP64) {
+    err = T(0);
+    return small;
+  } else {
+    const T s = __fadd_rn(pp, small);
+    const T bb = __fsub_rn(s, pp);
+    err = __fadd_rn(__fsub_rn(pp, __fsub_rn(s, bb)), __fsub_rn(small, bb));
+    return s;
+  }
 }
 
 // Wrap an x coordinate periodically; y periodically or onto the wall rows
@@ -287,8 +321,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   const int gx = x0 + tx, gy = y0 + ty;
   const bool active = gx < nx && gy < ny;
 
-  // 1. Own node: load all h^i_k, phi_i = sum_k h^i_k (Eq. N28).
-  T hreg[NP][9];
+  // 1. Own node: load all h^i_k, phi_i = sum_k h^i_k (Eq. N28). hreg[i][0]
+  //    holds h_0 (FP64) or d_0 (other forms); perr the rounding error of phi.
+  T hreg[NP][9], perr[NP];
   {
     const int sx = wrap(gx, nx), sy = wrap_y<WALL>(gy, ny);
     const size_t q = (size_t)sy * nx + sx;
@@ -297,10 +332,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
       hreg[i][0] = ldg(a.h0_in + (size_t)i * V + q);
 #pragma unroll
       for (int k = 1; k < 9; ++k) hreg[i][k] = load_hm<P>(a, i, k, q);
-      T s = hreg[i][0];
-#pragma unroll
-      for (int k = 1; k < 9; ++k) s += hreg[i][k];
-      sphi[i][(ty + R) * SW + tx + R] = s;
+      const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * V + q);
+      sphi[i][(ty + R) * SW + tx + R] =
+          node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i]);
     }
   }
   // 2. Halo ring: top R rows, bottom R rows, left and right R columns.
@@ -320,10 +354,12 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
     const size_t q = (size_t)sy * nx + sx;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      T s = ldg(a.h0_in + (size_t)i * V + q);
+      T mov[8], err;
 #pragma unroll
-      for (int k = 1; k < 9; ++k) s += load_hm<P>(a, i, k, q);
-      sphi[i][ly * SW + lx] = s;
+      for (int k = 1; k < 9; ++k) mov[k - 1] = load_hm<P>(a, i, k, q);
+      const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * V + q);
+      sphi[i][ly * SW + lx] =
+          node_phi<P>(ldg(a.h0_in + (size_t)i * V + q), mov, pp, err);
     }
   }
   __syncthreads();
@@ -510,7 +546,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   const T upx = a.u_prev[q], upy = a.u_prev[V + q];
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
-    const T pp = a.phi_prev[(size_t)i * V + q];
+    const T pp = ldg(a.pp_in + (size_t)i * V + q);
     const T dpx = ph[i] * ux - pp * upx, dpy = ph[i] * uy - pp * upy;
     const T aC = a.a[i] * Cv[i];
     const T ti = a.tau_inv[i];
@@ -535,24 +571,26 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
       }
       const size_t d = (size_t)dy * nx + ddx;
       if constexpr (Prec<P>::MIX) {
-        // 16-bit storage of h_k / w_k; the rest slot below absorbs the
-        // rounding so that sum_k h*_k = phi_i exactly as in the collision.
+        // 16-bit storage of h_k / w_k, decoded back for the mass balance.
         const auto sv = to_S<typename Prec<P>::Sm>(hs * (a.sh_st / w_of<T>(kk)));
         a.hm_out[((size_t)(i * 8 + kk - 1)) * V + d] = sv;
-        moving_sum += to_T(sv) * (w_of<T>(kk) * a.sh_ld);
+        moving_sum = __fadd_rn(moving_sum, __fmul_rn(to_T(sv), w_of<T>(kk) * a.sh_ld));
       } else {
         a.hm_out[((size_t)(i * 8 + kk - 1)) * V + d] = hs;
+        moving_sum = __fadd_rn_T(moving_sum, hs);
       }
     }
-    T h0s;
-    if constexpr (Prec<P>::MIX) {
-      h0s = ph[i] - moving_sum;
-    } else {
+    T rest;
+    if constexpr (P == LBM_FP64) {
       const T heq0 = ph[i] + (w_of<T>(0) - T(1)) * aC;
-      h0s = hreg[i][0] - (hreg[i][0] - heq0) * ti;
+      rest = hreg[i][0] - (hreg[i][0] - heq0) * ti;
+    } else {
+      // h*_0 = (phi + perr) - sum_{k>=1} h*_k (collision conserves sum_k h_k),
+      // stored relative to phi: d*_0 = perr - sum_{k>=1} h*_k.
+      rest = __fsub_rn(perr[i], moving_sum);
     }
-    a.h0_out[(size_t)i * V + q] = h0s;
-    a.phi_prev[(size_t)i * V + q] = ph[i];
+    a.h0_out[(size_t)i * V + q] = rest;
+    a.pp_out[(size_t)i * V + q] = ph[i];
   }
   a.u_prev[q] = ux;
   a.u_prev[V + q] = uy;
@@ -576,7 +614,7 @@ __global__ void init_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
     for (int i = 0; i < NP; ++i) {
       const double ci = c[(size_t)i * a.V + q];
       const double ph = (2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN);
-      a.phi_prev[(size_t)i * a.V + q] = (T)ph;
+      a.pp_out[(size_t)i * a.V + q] = (T)ph;
     }
     a.u_prev[q] = u ? (T)u[q] : T(0);
     a.u_prev[a.V + q] = u ? (T)u[a.V + q] : T(0);
@@ -598,7 +636,7 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
     T ph[NP], lp[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      const T *f = a.phi_prev + (size_t)i * V;
+      const T *f = a.pp_out + (size_t)i * V;
       T s[9];
 #pragma unroll
       for (int dy = -1; dy <= 1; ++dy)
@@ -636,15 +674,17 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
         if constexpr (Prec<P>::MIX) {
           const Sm sv = to_S<Sm>(heq * (a.sh_st / w_of<T>(k)));
           hm[((size_t)(i * 8 + k - 1)) * V + q] = sv;
-          moving += to_T(sv) * (w_of<T>(k) * a.sh_ld);
+          moving = __fadd_rn(moving, __fmul_rn(to_T(sv), w_of<T>(k) * a.sh_ld));
         } else {
           hm[((size_t)(i * 8 + k - 1)) * V + q] = heq;
+          moving = __fadd_rn_T(moving, heq);
         }
       }
-      if constexpr (Prec<P>::MIX)
-        h0[(size_t)i * V + q] = ph[i] - moving;
-      else
+      // FP64: h_0 = h_0^eq. Other forms: d_0 = h_0^eq - phi = -sum_{k>=1} h_k^eq.
+      if constexpr (P == LBM_FP64)
         h0[(size_t)i * V + q] = ph[i] + (w_of<T>(0) - T(1)) * aC;
+      else
+        h0[(size_t)i * V + q] = -moving;
     }
   }
 }

@@ -193,7 +193,9 @@ def test_full_size_n5_2048_fp32():
     g = gpu_run(w, 2)
     o = oracle_run(w, 2)
     assert maxdiff(g["phi"], o["phi"]) <= 2e-6
-    assert maxdiff(g["u"], o["u"]) <= 1e-9
+    # u comes from F = sum C_i grad phi_i, where C_i holds a Laplacian of
+    # FP32-rounded phi (cancellation ~ 1e3 x the FP32 unit roundoff).
+    assert maxdiff(g["u"], o["u"]) <= 1e-4 * np.abs(o["u"]).max()
     np.testing.assert_allclose(g["c"].sum(0), 1.0, atol=1e-6)
 
 
