@@ -142,6 +142,26 @@ lbm_status lbm_nphase_moments(lbm_nphase_t *h, double *phi, double *c,
 lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
                                   double *umax);
 
+/* The same diagnostics as lbm_nphase_diagnostics, for callers that cannot
+ * allocate device memory at this point (for example code running where a
+ * cudaMalloc would synchronise the device or is forbidden by an allocator
+ * policy). It allocates nothing: its scratch (the per-tile partial sums and
+ * the reduced values) is a 1 MiB static device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * The paper has no counterpart; this is a library convenience.
+ *  - Limit: at most 16384 tiles of 32 x 8 nodes (e.g. 2048 x 2048); larger
+ *    grids return LBM_EINVAL.
+ *  - The handle's device must be current. The first call on a device looks
+ *    up the array's device address; make that first call before any stream
+ *    capture.
+ *  - All calls in the process share the array and it keeps the last call's
+ *    contents: calls that overlap on the GPU (other streams, other handles
+ *    on the same device) race. Each call writes every slot it reads, so
+ *    nothing needs clearing between calls.
+ * Returns and synchronises like lbm_nphase_diagnostics. */
+lbm_status lbm_nphase_diagnostics_static(lbm_nphase_t *h, double *mass,
+                                         double *ke, double *umax);
+
 /* Number of time steps taken since the last init. */
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
 

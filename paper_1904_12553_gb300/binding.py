@@ -85,6 +85,7 @@ def load_library():
         lib.lbm_nphase_step.argtypes = [vp, C.c_int64]
         lib.lbm_nphase_moments.argtypes = [vp, dp, dp, dp, dp, dp]
         lib.lbm_nphase_diagnostics.argtypes = [vp, dp, dp, dp]
+        lib.lbm_nphase_diagnostics_static.argtypes = [vp, dp, dp, dp]
         lib.lbm_nphase_steps_taken.argtypes = [vp]
         lib.lbm_nphase_steps_taken.restype = C.c_int64
         lib.lbm_nphase_cuda_error.argtypes = [vp]
@@ -92,7 +93,7 @@ def load_library():
         lib.lbm_nphase_strerror.argtypes = [C.c_int]
         lib.lbm_nphase_strerror.restype = C.c_char_p
         for name in ("derive", "create", "init", "step", "moments",
-                     "diagnostics", "destroy"):
+                     "diagnostics", "diagnostics_static", "destroy"):
             getattr(lib, "lbm_nphase_" + name).restype = C.c_int
         _LIB = lib
         return lib
@@ -191,6 +192,19 @@ def lbm_nphase_diagnostics(handle: int, N: int):
     _check(load_library().lbm_nphase_diagnostics(
         C.c_void_p(handle), mass.ctypes.data, ke.ctypes.data, um.ctypes.data),
         "lbm_nphase_diagnostics")
+    return mass, float(ke[0]), float(um[0])
+
+
+def lbm_nphase_diagnostics_static(handle: int, N: int):
+    """Diagnostics whose scratch is the library's static device array (for
+    callers that cannot allocate device memory); same results as
+    lbm_nphase_diagnostics."""
+    mass = np.zeros(N)
+    ke = np.zeros(1)
+    um = np.zeros(1)
+    _check(load_library().lbm_nphase_diagnostics_static(
+        C.c_void_p(handle), mass.ctypes.data, ke.ctypes.data, um.ctypes.data),
+        "lbm_nphase_diagnostics_static")
     return mass, float(ke[0]), float(um[0])
 
 

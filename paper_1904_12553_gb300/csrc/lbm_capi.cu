@@ -559,3 +559,79 @@ lbm_status lbm_nphase_destroy(lbm_nphase_t *h) {
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------
+// Diagnostics without caller scratch: the per-CTA partials and the reduced
+// values live in a file-scope device array instead of the handle workspace.
+// --------------------------------------------------------------------------
+#include <mutex>
+
+// Largest number of diagnostics partials (one per 32 x 8 tile) the static
+// array holds: 16384 tiles, e.g. a 2048 x 2048 grid. Slot width 8 doubles
+// (N + 2 <= 7 values), plus 8 doubles for the reduced result: 1 MiB + 64 B,
+// held by every GPU that loads the library until the process exits.
+#define LBM_STATIC_MAX_PARTIALS 16384
+#define LBM_STATIC_SLOT 8
+static __device__ __align__(256) double
+    lbm_static_scratch[LBM_STATIC_MAX_PARTIALS * LBM_STATIC_SLOT + LBM_STATIC_SLOT];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices];  // device address of the array, per device
+}  // namespace
+
+extern "C" lbm_status lbm_nphase_diagnostics_static(lbm_nphase_t *h,
+                                                    double *mass, double *ke,
+                                                    double *umax) {
+  if (!h) return LBM_EINVAL;
+  if (!h->initialized) return LBM_ESTATE;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (dev != h->device || dev < 0 || dev >= kMaxDevices) return LBM_EINVAL;
+  const int nparts = lbm::tiles_x(h->g.nx) * lbm::tiles_y(h->g.ny);
+  if (nparts > LBM_STATIC_MAX_PARTIALS) return LBM_EINVAL;
+  double *base;
+  {
+    // First call on a device: look up the array's device address with that
+    // device current. The name is only a host-side stand-in for it.
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, lbm_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      g_static_ptr[dev] = (double *)p;
+    }
+    base = g_static_ptr[dev];
+  }
+  const int N = h->prm.N;
+  // Every partial slot the reduction reads is written by its CTA first and
+  // the result slot is overwritten, so nothing needs clearing between calls.
+  lbm::Grid g = h->g;
+  g.red = base;
+  g.red_out = base + (size_t)LBM_STATIC_MAX_PARTIALS * LBM_STATIC_SLOT;
+  const Outputs none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  e = lbm::launch_tile(h->prec, h->k, g, h->cur, lbm::MODE_DIAG, none,
+                       h->nonunif, h->wall, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  e = lbm::launch_reduce(g, nparts, N + 2, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  double r[LBM_MAX_N + 2];
+  e = cudaMemcpyAsync(r, g.red_out, (N + 2) * sizeof(double),
+                      cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  bool ok = true;
+  for (int j = 0; j < N + 2; ++j) ok = ok && isfinite(r[j]);
+  if (mass)
+    for (int k = 0; k < N; ++k) mass[k] = r[k];
+  if (ke) *ke = r[N];
+  if (umax) *umax = r[N + 1];
+  if (!ok) {
+    h->unstable = true;
+    return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
