@@ -186,8 +186,9 @@ def time_form(w, prec, steps, warmup, dist=None):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     mass, ke, _ = s.diagnostics()
+    kernel = "pipelined (TMA)" if s.pipelined else "generic tile"
     s.close()
-    return ms, (wall0, wall1), mass, ke
+    return ms, (wall0, wall1), mass, ke, kernel
 
 
 def e2e_run(w, prec, steps):
@@ -265,8 +266,8 @@ def run_ours(args, dist, rank, world):
     w = make_workload("fp32", n=args.n, accept=accept_sigma(5))
     N, V = w.params["N"], w.V
     sampler = ClockSampler(local) if rank == 0 else None
-    ms, (wa, wb), mass, ke = time_form(w, "fp32", args.steps, args.warmup,
-                                       dist)
+    ms, (wa, wb), mass, ke, kernel = time_form(w, "fp32", args.steps,
+                                               args.warmup, dist)
     if sampler:
         sampler.mark(wa, wb)
     clocks = sampler.stop() if sampler else None
@@ -282,6 +283,7 @@ def run_ours(args, dist, rank, world):
                           "n_gpus": world, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": ms_step,
                           "kernel_only": True, "nx": w.params["nx"],
+                          "kernel": kernel,
                           "hbm_frac": B * V / (ms_step / 1e3) / 1e9 / peak,
                           "clocks": clocks}), flush=True)
         return
@@ -289,12 +291,13 @@ def run_ours(args, dist, rank, world):
     if not args.quick:
         for prec, k in (("bf16", args.steps), ("fp16", args.steps),
                         ("fp64", max(10, args.steps // 20))):
-            fms, _, fmass, _ = time_form(w, prec, k, min(args.warmup, 5))
+            fms, _, fmass, _, fkernel = time_form(w, prec, k,
+                                                  min(args.warmup, 5))
             fstep = fms / k
             fB = alg_bytes_per_node(N, prec)
             forms[prec] = {
                 "mlups": V / (fstep / 1e3) / 1e6, "ms_per_step": fstep,
-                "alg_bytes_per_node": fB,
+                "alg_bytes_per_node": fB, "kernel": fkernel,
                 "hbm_frac": fB * V / (fstep / 1e3) / 1e9 / peak}
     e2e_v, h2d, d2h = e2e_run(w, "fp32", args.steps)
     cpu = cpu_baseline() if (world == 1 and not args.quick) else None
@@ -307,7 +310,8 @@ def run_ours(args, dist, rank, world):
                    "ny": w.params["ny"], "precision": "fp32", "seed": SEED,
                    "l2": "state (%.2f GB) larger than L2, no flush"
                          % (B / 2 * V / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "kernel": kernel},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind,

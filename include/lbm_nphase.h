@@ -45,7 +45,8 @@ typedef enum {
   LBM_EINVAL = 1,    /* invalid argument or parameter set */
   LBM_ENOMEM = 2,    /* workspace too small */
   LBM_ECUDA = 3,     /* a CUDA call failed (see lbm_nphase_cuda_error) */
-  LBM_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  LBM_ETIMEOUT = 4,  /* a bounded device wait gave up (reported by the next
+                        lbm_nphase_moments or lbm_nphase_diagnostics) */
   LBM_EUNSTABLE = 5, /* non-finite mass or kinetic energy detected */
   LBM_ESTATE = 6     /* call not valid in the handle's current state */
 } lbm_status;
@@ -164,6 +165,13 @@ lbm_status lbm_nphase_diagnostics_static(lbm_nphase_t *h, double *mass,
 
 /* Number of time steps taken since the last init. */
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
+
+/* 1 if lbm_nphase_step runs the TMA-pipelined kernel for this handle (FP32
+ * and 16-bit forms, equal pure-phase densities, nx a multiple of 8), 0 if it
+ * runs the generic tile kernel. Setting the environment variable
+ * LBM_NPHASE_KERNEL=generic before lbm_nphase_create selects the generic
+ * kernel everywhere. Both compute the same step. */
+int lbm_nphase_uses_pipelined_kernel(const lbm_nphase_t *h);
 
 /* The last CUDA error code seen by the handle (0 if none). */
 int lbm_nphase_cuda_error(const lbm_nphase_t *h);

@@ -89,6 +89,8 @@ def load_library():
         lib.lbm_nphase_steps_taken.argtypes = [vp]
         lib.lbm_nphase_steps_taken.restype = C.c_int64
         lib.lbm_nphase_cuda_error.argtypes = [vp]
+        lib.lbm_nphase_uses_pipelined_kernel.argtypes = [vp]
+        lib.lbm_nphase_uses_pipelined_kernel.restype = C.c_int
         lib.lbm_nphase_destroy.argtypes = [vp]
         lib.lbm_nphase_strerror.argtypes = [C.c_int]
         lib.lbm_nphase_strerror.restype = C.c_char_p
@@ -212,6 +214,11 @@ def lbm_nphase_steps_taken(handle: int) -> int:
     return int(load_library().lbm_nphase_steps_taken(C.c_void_p(handle)))
 
 
+def lbm_nphase_uses_pipelined_kernel(handle: int) -> bool:
+    return bool(load_library().lbm_nphase_uses_pipelined_kernel(
+        C.c_void_p(handle)))
+
+
 def lbm_nphase_destroy(handle: int):
     load_library().lbm_nphase_destroy(C.c_void_p(handle))
 
@@ -291,6 +298,10 @@ class Solver:
 
     def diagnostics(self):
         return lbm_nphase_diagnostics(self.handle, self.N)
+
+    @property
+    def pipelined(self) -> bool:
+        return lbm_nphase_uses_pipelined_kernel(self.handle)
 
     @property
     def steps_taken(self) -> int:

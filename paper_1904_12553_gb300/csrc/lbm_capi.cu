@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -170,7 +171,7 @@ lbm_status validate(const lbm_nphase_params *p) {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t h0, hm, gm, phi_prev, u_prev, stage, red, red_out, total;
+  size_t h0, hm, gm, phi_prev, u_prev, stage, red, red_out, err, total;
 };
 
 Layout layout(const lbm_nphase_params *p) {
@@ -189,6 +190,7 @@ Layout layout(const lbm_nphase_params *p) {
   L.stage = off;    off += align256((p->N + 2) * V * 8);
   L.red = off;      off += align256(tiles * (p->N + 2) * 8);
   L.red_out = off;  off += align256(8 * 8);
+  L.err = off;      off += align256(sizeof(int));
   L.total = off;
   return L;
 }
@@ -205,6 +207,48 @@ bool is_device_ptr(const void *ptr) {
 lbm_status cuda_fail(lbm_nphase_t *h, cudaError_t e) {
   h->cuda_err = (int)e;
   return LBM_ECUDA;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime.
+lbm::EncodeTiledFn tensor_map_encoder() {
+  static lbm::EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (lbm::EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Which step kernel to use: the pipelined TMA kernel where it applies
+// (default), or the generic tile kernel everywhere when the environment
+// variable LBM_NPHASE_KERNEL is "generic".
+bool tma_allowed() {
+  const char *v = getenv("LBM_NPHASE_KERNEL");
+  return !(v && strcmp(v, "generic") == 0);
+}
+
+// Device error word: read and clear. Returns LBM_ETIMEOUT if a kernel's
+// bounded wait gave up since the last check.
+lbm_status check_err(lbm_nphase_t *h) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->g.err, sizeof(int),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (v != 0) {
+    cudaMemsetAsync(h->g.err, 0, sizeof(int), h->stream);
+    h->unstable = true;
+    return LBM_ETIMEOUT;
+  }
+  return LBM_OK;
 }
 
 }  // namespace
@@ -422,6 +466,17 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   h->stage = (double *)(base + L.stage);
   g.red = (double *)(base + L.red);
   g.red_out = (double *)(base + L.red_out);
+  g.err = (int *)(base + L.err);
+  g.use_tma = false;
+  if (tma_allowed() && !h->nonunif) {
+    lbm::EncodeTiledFn enc = tensor_map_encoder();
+    switch (h->prec) {
+      case LBM_FP32: g.use_tma = lbm::encode_tma_f32(k, g, enc); break;
+      case LBM_MIX_BF16: g.use_tma = lbm::encode_tma_bf16(k, g, enc); break;
+      case LBM_MIX_FP16: g.use_tma = lbm::encode_tma_f16(k, g, enc); break;
+      default: break;
+    }
+  }
   *out = h;
   return LBM_OK;
 }
@@ -445,6 +500,8 @@ lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
     if (e != cudaSuccess) return cuda_fail(h, e);
     du = h->stage + N * V;
   }
+  e = cudaMemsetAsync(h->g.err, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
   e = lbm::launch_init(h->prec, h->k, h->g, 0, dc, du, p0, h->wall, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   e = cudaStreamSynchronize(h->stream);
@@ -515,7 +572,7 @@ lbm_status lbm_nphase_moments(lbm_nphase_t *h, double *phi, double *c,
   }
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  return LBM_OK;
+  return check_err(h);
 }
 
 lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
@@ -542,11 +599,17 @@ lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
     for (int k = 0; k < N; ++k) mass[k] = r[k];
   if (ke) *ke = r[N];
   if (umax) *umax = r[N + 1];
+  const lbm_status es = check_err(h);
+  if (es != LBM_OK) return es;
   if (!ok) {
     h->unstable = true;
     return LBM_EUNSTABLE;
   }
   return LBM_OK;
+}
+
+int lbm_nphase_uses_pipelined_kernel(const lbm_nphase_t *h) {
+  return h && h->g.use_tma ? 1 : 0;
 }
 
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h) { return h ? h->steps : 0; }

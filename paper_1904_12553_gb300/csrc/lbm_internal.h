@@ -2,6 +2,7 @@
 // kernel translation units. Not part of the public API.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap and its enums (types only; no driver link)
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -39,6 +40,18 @@ struct Consts {
   double sh, sg;       // 16-bit storage scales of h_k / w_k and g_k / w_k
 };
 
+// TMA descriptors of one state buffer for the pipelined step kernel.
+struct TmaMaps {
+  CUtensorMap hm, h0, pp, gm, up;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType,
+                                  cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
 // Device state of one grid. Buffers [0] and [1] alternate every step.
 struct Grid {
   int nx, ny;
@@ -50,6 +63,9 @@ struct Grid {
   void *u_prev;     // u(t-1): [2][V]
   double *red;      // per-block partial sums of the diagnostics
   double *red_out;  // N + 2 reduced diagnostics
+  int *err;         // device error word (1: a bounded wait gave up)
+  bool use_tma;     // pipelined kernel usable for this grid
+  TmaMaps tma[2];   // its descriptors, input buffer 0 or 1
 };
 
 struct Outputs {
@@ -71,7 +87,8 @@ cudaError_t launch_reduce(const Grid &g, int nparts, int nvals, cudaStream_t s);
                                    const Outputs &, bool, bool, cudaStream_t);\
   cudaError_t launch_init_##SUFFIX(const Consts &, const Grid &, int,         \
                                    const double *, const double *, double,    \
-                                   bool, cudaStream_t);
+                                   bool, cudaStream_t);                       \
+  bool encode_tma_##SUFFIX(const Consts &, Grid &, EncodeTiledFn);
 LBM_DECLARE_PREC(f64)
 LBM_DECLARE_PREC(f32)
 LBM_DECLARE_PREC(bf16)

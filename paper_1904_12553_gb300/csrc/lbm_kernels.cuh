@@ -106,6 +106,7 @@ template <int P> struct KArgs {
   T *pp_out;       // phi_prev for the next step (phi at t)
   T *u_prev;
   double *o_phi, *o_c, *o_u, *o_p, *o_rho, *red;
+  int *err;
   int mode;
   T lam[4][4], bulk, a[4], tau_inv[4], src[4], tg_inv, ffac, jfac, grav[2];
   T off[4], mul[4], c0[5], Q[5][4], rho_base, K[4], kap[4], kmob[4];
@@ -136,6 +137,7 @@ KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
   a.o_p = o.p;
   a.o_rho = o.rho;
   a.red = g.red;
+  a.err = g.err;
   a.mode = mode;
   for (int i = 0; i < 4; ++i) {
     for (int j = 0; j < 4; ++j) a.lam[i][j] = (T)c.lam[i][j];
@@ -301,8 +303,226 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// The fused tile kernel (MODE_STEP: one time step; MODE_MOMENTS: write the
-// macroscopic fields; MODE_DIAG: per-CTA partial sums of the diagnostics).
+// Per-node work shared by the kernels.
+// ---------------------------------------------------------------------------
+
+// Macroscopic quantities of one node at time t (steps a2-a6).
+template <int P, int NP> struct NodeMac {
+  typedef typename Prec<P>::T T;
+  T ph[NP], gpx[NP], gpy[NP], Cv[NP], cc[NP + 1];
+  T rho, grx, gry, Jx, Jy, Fx, Fy, ux, uy, uu, ugr, pr;
+};
+
+// phi and its stencils from the shared tile (centre ly, lx), C_i (from the
+// shared C tile when densities differ), J~ and grad rho, F, u (Eq. N22_1)
+// and p (Eq. N23). g[1..8] are the node's NS populations.
+template <int P, int NP, bool NU, int SW, int CW>
+__device__ __forceinline__ void node_macros(const KArgs<P> &a,
+                                            const typename Prec<P>::T *sphi,
+                                            int plane, const typename Prec<P>::T *sC,
+                                            int cplane, int ly, int lx, int cly,
+                                            int clx, const typename Prec<P>::T *g,
+                                            NodeMac<P, NP> &m) {
+  typedef typename Prec<P>::T T;
+  {
+    T lp[NP], hf[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      m.ph[i] = sphi[i * plane + ly * SW + lx];
+      stencil<T, SW>(sphi + i * plane, ly, lx, m.gpx[i], m.gpy[i], lp[i]);
+    }
+    local_algebra<P, NP>(a, m.ph, m.cc, m.rho, hf);
+    if constexpr (NU) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) m.Cv[i] = sC[i * cplane + cly * CW + clx];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T Ci = a.bulk * hf[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+        m.Cv[i] = Ci;
+      }
+    }
+  }
+  m.grx = T(0); m.gry = T(0); m.Jx = T(0); m.Jy = T(0);
+  if constexpr (NU) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T cgx, cgy;
+      gradient<T, CW>(sC + i * cplane, cly, clx, cgx, cgy);
+      m.Jx -= a.kmob[i] * cgx;
+      m.Jy -= a.kmob[i] * cgy;
+      m.grx += a.kap[i] * m.gpx[i];
+      m.gry += a.kap[i] * m.gpy[i];
+    }
+  }
+  m.Fx = m.rho * a.grav[0];
+  m.Fy = m.rho * a.grav[1];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    m.Fx += m.Cv[i] * m.gpx[i];
+    m.Fy += m.Cv[i] * m.gpy[i];
+  }
+  T mx = T(0), my = T(0), sg = T(0);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    mx += T(cx_of(k)) * g[k];
+    my += T(cy_of(k)) * g[k];
+    sg += g[k];
+  }
+  const T rinv = T(1) / m.rho;
+  m.ux = (mx + T(0.5) * m.Fx) * rinv;
+  m.uy = (my + T(0.5) * m.Fy) * rinv;
+  m.uu = m.ux * m.ux + m.uy * m.uy;
+  m.ugr = m.ux * m.grx + m.uy * m.gry;
+  // Eq. N23: c_s^2/(1-w_0) = 3/5; s_0(u) = -w_0 |u|^2 / (2 c_s^2)
+  m.pr = T(0.6) * (sg + T(0.5) * m.ugr - m.rho * T(4.0 / 9.0) * T(1.5) * m.uu);
+}
+
+// Collisions and push streaming of one node (steps a7-a10). hreg[i][0] is
+// h_0 (FP64) or d_0 (other forms), hreg[i][1..8] the moving populations,
+// perr the rounding error of phi, pp phi_i(t-1), up u(t-1).
+template <int P, int NP, bool NU, bool WALL>
+__device__ __forceinline__ void collide_stream(
+    const KArgs<P> &a, const NodeMac<P, NP> &m,
+    const typename Prec<P>::T (&hreg)[NP][9], const typename Prec<P>::T *perr,
+    const typename Prec<P>::T *g, const typename Prec<P>::T *pp,
+    typename Prec<P>::T upx, typename Prec<P>::T upy, int gx, int gy) {
+  typedef typename Prec<P>::T T;
+  const int nx = a.nx, ny = a.ny;
+  const size_t V = a.V;
+  const size_t q = (size_t)gy * nx + gx;
+  const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+  const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
+  // Destination node and direction of population k after streaming.
+  size_t dst[9];
+  int dk[9];
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    const int cxi = cx_of(k), cyi = cy_of(k);
+    int dx = cxi == 0 ? gx : (cxi > 0 ? xp : xm);
+    int dy = cyi == 0 ? gy : (cyi > 0 ? yp : ym);
+    dk[k] = k;
+    if (WALL && ((cyi < 0 && gy == 0) || (cyi > 0 && gy == ny - 1))) {
+      dy = gy;
+      dx = gx;
+      dk[k] = opp_of(k);
+    }
+    dst[k] = (size_t)dy * nx + dx;
+  }
+  const T ux = m.ux, uy = m.uy, uu = m.uu, ugr = m.ugr, rho = m.rho;
+  const T Fx = m.Fx, Fy = m.Fy, pr = m.pr;
+
+  // NS collision (Eq. 24) with g^eq (Eq. 25) and G_k (Eq. N20_1).
+  const T uF = ux * Fx + uy * Fy;
+  const T Ju = (m.Jx * ux + m.Jy * uy) * a.jfac;
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
+    const T wk = w_of<T>(k);
+    const T cu = cxk * ux + cyk * uy;
+    const T cF = cxk * Fx + cyk * Fy;
+    const T geq = wk * (T(3) * pr + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    // (c c - c_s^2 I) : T / (2 c_s^4) with T = uF + Fu + c_s^2 (u grad rho +
+    // grad rho u) + J~u / (tau_g - 1/2)
+    T QT = T(2) * cu * cF - T(2.0 / 3.0) * uF;
+    if constexpr (NU) {
+      const T cr = cxk * m.grx + cyk * m.gry;
+      const T cJ = cxk * m.Jx + cyk * m.Jy;
+      QT += T(2.0 / 3.0) * cu * cr - T(2.0 / 9.0) * ugr + cJ * cu * a.jfac -
+            T(1.0 / 3.0) * Ju;
+    }
+    const T Gk = wk * (ugr + T(3) * cF + T(4.5) * QT);
+    const T gs = g[k] - (g[k] - geq) * a.tg_inv + a.ffac * Gk;
+    const int kk = dk[k];
+    if constexpr (Prec<P>::MIX)
+      a.gm_out[(size_t)(kk - 1) * V + dst[k]] =
+          to_S<typename Prec<P>::Sm>(gs * (a.sg_st / w_of<T>(kk)));
+    else
+      a.gm_out[(size_t)(kk - 1) * V + dst[k]] = gs;
+  }
+
+  // CH collisions (Eq. N24) with h^eq (Eq. N25) and R_k (Eqs. N26, N27).
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const T ph = m.ph[i];
+    const T dpx = ph * ux - pp[i] * upx, dpy = ph * uy - pp[i] * upy;
+    const T aC = a.a[i] * m.Cv[i];
+    const T ti = a.tau_inv[i];
+    const T sr = a.src[i] * T(3);
+    T moving_sum = T(0);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+      const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
+      const T wk = w_of<T>(k);
+      const T heq = wk * (aC + T(3) * ph * (cxk * ux + cyk * uy));
+      const T Rk = sr * wk * (cxk * dpx + cyk * dpy);
+      const T hs = hreg[i][k] - (hreg[i][k] - heq) * ti + Rk;
+      const int kk = dk[k];
+      if constexpr (Prec<P>::MIX) {
+        // 16-bit storage of h_k / w_k, decoded back for the mass balance.
+        const auto sv = to_S<typename Prec<P>::Sm>(hs * (a.sh_st / w_of<T>(kk)));
+        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = sv;
+        moving_sum = __fadd_rn(moving_sum, __fmul_rn(to_T(sv), w_of<T>(kk) * a.sh_ld));
+      } else {
+        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = hs;
+        moving_sum = __fadd_rn_T(moving_sum, hs);
+      }
+    }
+    T rest;
+    if constexpr (P == LBM_FP64) {
+      const T heq0 = ph + (w_of<T>(0) - T(1)) * aC;
+      rest = hreg[i][0] - (hreg[i][0] - heq0) * ti;
+    } else {
+      // h*_0 = (phi + perr) - sum_{k>=1} h*_k (collision conserves sum_k h_k),
+      // stored relative to phi: d*_0 = perr - sum_{k>=1} h*_k.
+      rest = __fsub_rn(perr[i], moving_sum);
+    }
+    a.h0_out[(size_t)i * V + q] = rest;
+    a.pp_out[(size_t)i * V + q] = ph;
+  }
+  a.u_prev[q] = ux;
+  a.u_prev[V + q] = uy;
+}
+
+// Position of ring entry r of a (BX + 2R) x (BY + 2R) tile: top R rows,
+// bottom R rows, left R columns, right R columns.
+template <int R>
+__device__ __forceinline__ void ring_pos(int r, int &lx, int &ly) {
+  constexpr int SW = BX + 2 * R;
+  if (r < R * SW) {
+    ly = r / SW; lx = r % SW;
+  } else if (r < 2 * R * SW) {
+    const int t = r - R * SW; ly = R + BY + t / SW; lx = t % SW;
+  } else if (r < 2 * R * SW + R * BY) {
+    const int t = r - 2 * R * SW; ly = R + t / R; lx = t % R;
+  } else {
+    const int t = r - 2 * R * SW - R * BY; ly = R + t / R; lx = R + BX + t % R;
+  }
+}
+
+// phi_i at node (sx, sy) from global memory.
+template <int P, int NP>
+__device__ __forceinline__ void phi_global(const KArgs<P> &a, int sx, int sy,
+                                           typename Prec<P>::T *out, int plane,
+                                           int idx) {
+  typedef typename Prec<P>::T T;
+  const size_t q = (size_t)sy * a.nx + sx;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    T mov[8], err;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) mov[k - 1] = load_hm<P>(a, i, k, q);
+    const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * a.V + q);
+    out[i * plane + idx] = node_phi<P>(ldg(a.h0_in + (size_t)i * a.V + q), mov, pp, err);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The generic tile kernel (every precision and density case; MODE_STEP: one
+// time step; MODE_MOMENTS: write the macroscopic fields; MODE_DIAG: per-CTA
+// partial sums of the diagnostics).
 // ---------------------------------------------------------------------------
 template <int P, int NP, bool NU, bool WALL>
 __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
@@ -337,30 +557,13 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
           node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i]);
     }
   }
-  // 2. Halo ring: top R rows, bottom R rows, left and right R columns.
+  // 2. Halo ring.
   constexpr int NRING = SW * SH - BX * BY;
   for (int r = tid; r < NRING; r += NT) {
     int lx, ly;
-    if (r < R * SW) {
-      ly = r / SW; lx = r % SW;
-    } else if (r < 2 * R * SW) {
-      int t = r - R * SW; ly = R + BY + t / SW; lx = t % SW;
-    } else if (r < 2 * R * SW + R * BY) {
-      int t = r - 2 * R * SW; ly = R + t / R; lx = t % R;
-    } else {
-      int t = r - 2 * R * SW - R * BY; ly = R + t / R; lx = R + BX + t % R;
-    }
-    const int sx = wrap(x0 - R + lx, nx), sy = wrap_y<WALL>(y0 - R + ly, ny);
-    const size_t q = (size_t)sy * nx + sx;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      T mov[8], err;
-#pragma unroll
-      for (int k = 1; k < 9; ++k) mov[k - 1] = load_hm<P>(a, i, k, q);
-      const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * V + q);
-      sphi[i][ly * SW + lx] =
-          node_phi<P>(ldg(a.h0_in + (size_t)i * V + q), mov, pp, err);
-    }
+    ring_pos<R>(r, lx, ly);
+    phi_global<P, NP>(a, wrap(x0 - R + lx, nx), wrap_y<WALL>(y0 - R + ly, ny),
+                      &sphi[0][0], SH * SW, ly * SW + lx);
   }
   __syncthreads();
 
@@ -401,79 +604,28 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   }
 
   // 4. Own node: stencils, C_i, forces, u, p.
-  const int ly = ty + R, lx = tx + R;
-  T ph[NP], gpx[NP], gpy[NP], Cv[NP];
-  T cc[NP + 1], rho;
-  {
-    T lp[NP], hf[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      ph[i] = sphi[i][ly * SW + lx];
-      stencil<T, SW>(sphi[i], ly, lx, gpx[i], gpy[i], lp[i]);
-    }
-    local_algebra<P, NP>(a, ph, cc, rho, hf);
-    if constexpr (NU) {
-#pragma unroll
-      for (int i = 0; i < NP; ++i) Cv[i] = sC[i][(ty + 1) * CW + tx + 1];
-    } else {
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T Ci = a.bulk * hf[i];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
-        Cv[i] = Ci;
-      }
-    }
-  }
-  T grx = T(0), gry = T(0), Jx = T(0), Jy = T(0);
-  if constexpr (NU) {
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      T cgx, cgy;
-      gradient<T, CW>(sC[i], ty + 1, tx + 1, cgx, cgy);
-      Jx -= a.kmob[i] * cgx;
-      Jy -= a.kmob[i] * cgy;
-      grx += a.kap[i] * gpx[i];
-      gry += a.kap[i] * gpy[i];
-    }
-  }
-  T Fx = rho * a.grav[0], Fy = rho * a.grav[1];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    Fx += Cv[i] * gpx[i];
-    Fy += Cv[i] * gpy[i];
-  }
   const size_t q = (size_t)(active ? gy : 0) * nx + (active ? gx : 0);
   T g[9];
-  T mx = T(0), my = T(0), sg = T(0);
 #pragma unroll
-  for (int k = 1; k < 9; ++k) {
-    g[k] = active ? load_gm<P>(a, k, q) : T(0);
-    mx += T(cx_of(k)) * g[k];
-    my += T(cy_of(k)) * g[k];
-    sg += g[k];
-  }
-  const T rinv = T(1) / rho;
-  const T ux = (mx + T(0.5) * Fx) * rinv, uy = (my + T(0.5) * Fy) * rinv;
-  const T uu = ux * ux + uy * uy;
-  const T ugr = ux * grx + uy * gry;
-  // Eq. N23: c_s^2/(1-w_0) = 3/5; s_0(u) = -w_0 |u|^2 / (2 c_s^2)
-  const T pr = T(0.6) * (sg + T(0.5) * ugr - rho * T(4.0 / 9.0) * T(1.5) * uu);
+  for (int k = 1; k < 9; ++k) g[k] = active ? load_gm<P>(a, k, q) : T(0);
+  NodeMac<P, NP> m;
+  node_macros<P, NP, NU, SW, CW>(a, &sphi[0][0], SH * SW, &sC[0][0], CH * CW,
+                                 ty + R, tx + R, ty + 1, tx + 1, g, m);
 
   if (a.mode == MODE_MOMENTS) {
     if (!active) return;
     if (a.o_phi)
 #pragma unroll
-      for (int i = 0; i < NP; ++i) a.o_phi[(size_t)i * V + q] = (double)ph[i];
+      for (int i = 0; i < NP; ++i) a.o_phi[(size_t)i * V + q] = (double)m.ph[i];
     if (a.o_c)
 #pragma unroll
-      for (int k = 0; k <= NP; ++k) a.o_c[(size_t)k * V + q] = (double)cc[k];
+      for (int k = 0; k <= NP; ++k) a.o_c[(size_t)k * V + q] = (double)m.cc[k];
     if (a.o_u) {
-      a.o_u[q] = (double)ux;
-      a.o_u[V + q] = (double)uy;
+      a.o_u[q] = (double)m.ux;
+      a.o_u[V + q] = (double)m.uy;
     }
-    if (a.o_p) a.o_p[q] = (double)pr;
-    if (a.o_rho) a.o_rho[q] = (double)rho;
+    if (a.o_p) a.o_p[q] = (double)m.pr;
+    if (a.o_rho) a.o_rho[q] = (double)m.rho;
     return;
   }
   if (a.mode == MODE_DIAG) {
@@ -483,9 +635,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 #pragma unroll
     for (int k = 0; k <= NP + 2; ++k) {
       double v;
-      if (k <= NP) v = active ? (double)cc[k] : 0.0;
-      else if (k == NP + 1) v = active ? 0.5 * (double)rho * (double)uu : 0.0;
-      else v = active ? sqrt((double)uu) : 0.0;
+      if (k <= NP) v = active ? (double)m.cc[k] : 0.0;
+      else if (k == NP + 1) v = active ? 0.5 * (double)m.rho * (double)m.uu : 0.0;
+      else v = active ? sqrt((double)m.uu) : 0.0;
       v = (k == NP + 2) ? warp_max(v) : warp_sum(v);
       if (lane == 0) sred[wid][k] = v;
     }
@@ -500,100 +652,239 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   }
   if (!active) return;
 
-  // 5. NS collision (Eq. 24) with g^eq (Eq. 25) and G_k (Eq. N20_1), then
-  //    push to x + c_k.
-  const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
-  const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
-  const T uF = ux * Fx + uy * Fy;
-  const T Ju = (Jx * ux + Jy * uy) * a.jfac;
+  // 5-6. Collisions and streaming.
+  T pp[NP];
 #pragma unroll
-  for (int k = 1; k < 9; ++k) {
-    const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
-    const T wk = w_of<T>(k);
-    const T cu = cxk * ux + cyk * uy;
-    const T cF = cxk * Fx + cyk * Fy;
-    const T geq = wk * (T(3) * pr + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-    // (c c - c_s^2 I) : T / (2 c_s^4) with T = uF + Fu + c_s^2 (u grad rho +
-    // grad rho u) + J~u / (tau_g - 1/2)
-    T QT = T(2) * cu * cF - T(2.0 / 3.0) * uF;
-    if constexpr (NU) {
-      const T cr = cxk * grx + cyk * gry;
-      const T cJ = cxk * Jx + cyk * Jy;
-      QT += T(2.0 / 3.0) * cu * cr - T(2.0 / 9.0) * ugr + cJ * cu * a.jfac -
-            T(1.0 / 3.0) * Ju;
-    }
-    const T Gk = wk * (ugr + T(3) * cF + T(4.5) * QT);
-    const T gs = g[k] - (g[k] - geq) * a.tg_inv + a.ffac * Gk;
-    // destination
-    const int cxi = cx_of(k), cyi = cy_of(k);
-    const int dx = cxi == 0 ? gx : (cxi > 0 ? xp : xm);
-    int dy = cyi == 0 ? gy : (cyi > 0 ? yp : ym);
-    int kk = k;
-    int ddx = dx;
-    if (WALL && ((cyi < 0 && gy == 0) || (cyi > 0 && gy == ny - 1))) {
-      dy = gy;
-      ddx = gx;
-      kk = opp_of(k);
-    }
-    const size_t d = (size_t)dy * nx + ddx;
-    if constexpr (Prec<P>::MIX)
-      a.gm_out[(size_t)(kk - 1) * V + d] = to_S<typename Prec<P>::Sm>(gs * (a.sg_st / w_of<T>(kk)));
-    else
-      a.gm_out[(size_t)(kk - 1) * V + d] = gs;
-  }
+  for (int i = 0; i < NP; ++i) pp[i] = ldg(a.pp_in + (size_t)i * V + q);
+  collide_stream<P, NP, NU, WALL>(a, m, hreg, perr, g, pp, a.u_prev[q],
+                                  a.u_prev[V + q], gx, gy);
+}
 
-  // 6. CH collisions (Eq. N24) with h^eq (Eq. N25) and R_k (Eqs. N26, N27).
-  const T upx = a.u_prev[q], upy = a.u_prev[V + q];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    const T pp = ldg(a.pp_in + (size_t)i * V + q);
-    const T dpx = ph[i] * ux - pp * upx, dpy = ph[i] * uy - pp * upy;
-    const T aC = a.a[i] * Cv[i];
-    const T ti = a.tau_inv[i];
-    const T sr = a.src[i] * T(3);
-    T moving_sum = T(0);
-#pragma unroll
-    for (int k = 1; k < 9; ++k) {
-      const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
-      const T wk = w_of<T>(k);
-      const T heq = wk * (aC + T(3) * ph[i] * (cxk * ux + cyk * uy));
-      const T Rk = sr * wk * (cxk * dpx + cyk * dpy);
-      T hs = hreg[i][k] - (hreg[i][k] - heq) * ti + Rk;
-      const int cxi = cx_of(k), cyi = cy_of(k);
-      const int dx = cxi == 0 ? gx : (cxi > 0 ? xp : xm);
-      int dy = cyi == 0 ? gy : (cyi > 0 ? yp : ym);
-      int kk = k;
-      int ddx = dx;
-      if (WALL && ((cyi < 0 && gy == 0) || (cyi > 0 && gy == ny - 1))) {
-        dy = gy;
-        ddx = gx;
-        kk = opp_of(k);
-      }
-      const size_t d = (size_t)dy * nx + ddx;
-      if constexpr (Prec<P>::MIX) {
-        // 16-bit storage of h_k / w_k, decoded back for the mass balance.
-        const auto sv = to_S<typename Prec<P>::Sm>(hs * (a.sh_st / w_of<T>(kk)));
-        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + d] = sv;
-        moving_sum = __fadd_rn(moving_sum, __fmul_rn(to_T(sv), w_of<T>(kk) * a.sh_ld));
-      } else {
-        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + d] = hs;
-        moving_sum = __fadd_rn_T(moving_sum, hs);
-      }
-    }
-    T rest;
-    if constexpr (P == LBM_FP64) {
-      const T heq0 = ph[i] + (w_of<T>(0) - T(1)) * aC;
-      rest = hreg[i][0] - (hreg[i][0] - heq0) * ti;
-    } else {
-      // h*_0 = (phi + perr) - sum_{k>=1} h*_k (collision conserves sum_k h_k),
-      // stored relative to phi: d*_0 = perr - sum_{k>=1} h*_k.
-      rest = __fsub_rn(perr[i], moving_sum);
-    }
-    a.h0_out[(size_t)i * V + q] = rest;
-    a.pp_out[(size_t)i * V + q] = ph[i];
+// ---------------------------------------------------------------------------
+// Pipelined step kernel for the FP32 and 16-bit forms with equal densities.
+//
+// Persistent CTAs walk the 32 x 8 tiles in raster order (tile b, b + grid,
+// ...). A ring of S shared-memory stages holds the populations of the next
+// tiles: one 3-D TMA box per array (all planes at once), the h and phi_prev
+// planes with a halo of one row and HX columns (HX * element size = 16 B,
+// the TMA alignment), completion counted on one mbarrier per stage. While a
+// tile is computed, the loads of the following S - 1 tiles are in flight.
+// Halo positions that wrap around the domain (periodic edges, wall ghost
+// rows, ragged tails) are summed from global memory instead.
+// ---------------------------------------------------------------------------
+template <int P> struct TmaGeom {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  static constexpr int HXM = 16 / (int)sizeof(Sm);  // halo columns, moving planes
+  static constexpr int HXR = 16 / (int)sizeof(T);   // halo columns, FP32 planes
+  static constexpr int WM = BX + 2 * HXM;           // box widths
+  static constexpr int WR = BX + 2 * HXR;
+  static constexpr int HB = BY + 2;                 // box height
+  static constexpr int S = sizeof(Sm) == 2 ? 3 : 2; // pipeline stages
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after ~2^22 polls (well over a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 16) __nanosleep(256);
   }
-  a.u_prev[q] = ux;
-  a.u_prev[V + q] = uy;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map,
+                                            int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int P, int NP> struct TmaStage {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  typedef TmaGeom<P> G;
+  static constexpr size_t al(size_t b) { return (b + 127) & ~(size_t)127; }
+  static constexpr size_t HM = al((size_t)8 * NP * G::HB * G::WM * sizeof(Sm));
+  static constexpr size_t H0 = al((size_t)NP * G::HB * G::WR * sizeof(T));
+  static constexpr size_t PP = H0;
+  static constexpr size_t GM = al((size_t)8 * BY * BX * sizeof(Sm));
+  static constexpr size_t UP = al((size_t)2 * BY * BX * sizeof(T));
+  static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
+  // bytes the TMA engine writes per stage (full boxes, including fill)
+  static constexpr uint32_t TX =
+      (uint32_t)((size_t)8 * NP * G::HB * G::WM * sizeof(Sm) +
+                 2 * (size_t)NP * G::HB * G::WR * sizeof(T) +
+                 (size_t)8 * BY * BX * sizeof(Sm) + (size_t)2 * BY * BX * sizeof(T));
+  static constexpr size_t SPHI = al((size_t)NP * (BY + 2) * (BX + 2) * sizeof(T));
+  static constexpr size_t SMEM = G::S * BYTES + SPHI + 64;
+};
+
+template <int P, int NP, bool WALL>
+__global__ void __launch_bounds__(NT, 1)
+    tile_kernel_tma(const KArgs<P> a, const __grid_constant__ TmaMaps maps,
+                    int ntx, int ntiles) {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  typedef TmaGeom<P> G;
+  typedef TmaStage<P, NP> St;
+  constexpr int S = G::S;
+  constexpr int SW = BX + 2, SH = BY + 2, PL = SW * SH;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T *sphi = (T *)(smem + S * St::BYTES);
+  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::SPHI);
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int nx = a.nx, ny = a.ny;
+  const int nmine = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  auto issue = [&](int j) {  // thread 0: TMA loads of my j-th tile
+    const int t = blockIdx.x + j * gridDim.x;
+    const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
+    unsigned char *st = smem + (j % S) * St::BYTES;
+    uint64_t *b = bar + (j % S);
+    mbar_expect_tx(b, St::TX);
+    tma_load_3d(st, &maps.hm, x0 - G::HXM, y0 - 1, 0, b);
+    tma_load_3d(st + St::HM, &maps.h0, x0 - G::HXR, y0 - 1, 0, b);
+    tma_load_3d(st + St::HM + St::H0, &maps.pp, x0 - G::HXR, y0 - 1, 0, b);
+    tma_load_3d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, 0, b);
+    tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0, y0, 0, b);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(bar + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int j = 0; j < S && j < nmine; ++j) issue(j);
+  }
+  __syncthreads();
+
+  int issued = nmine < S ? nmine : S;
+  int failed_at = -1;
+  for (int j = 0; j < nmine; ++j) {
+    const int t = blockIdx.x + j * gridDim.x;
+    const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
+    const unsigned char *st = smem + (j % S) * St::BYTES;
+    const Sm *shm = (const Sm *)st;
+    const T *sh0 = (const T *)(st + St::HM);
+    const T *spp = (const T *)(st + St::HM + St::H0);
+    const Sm *sgm = (const Sm *)(st + St::HM + St::H0 + St::PP);
+    const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
+    const bool ok = mbar_wait(bar + (j % S), (uint32_t)((j / S) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed_at = j;
+      break;
+    }
+
+    // phi on the tile and its ring. A position whose node lies inside the
+    // array without wrapping reads the staged box; others read global memory.
+    auto box_phi = [&](int bxm, int bxr, int by, T *err) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T mov[8];
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+          T x = to_T(shm[((i * 8 + k - 1) * G::HB + by) * G::WM + bxm]);
+          if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sh_ld);
+          mov[k - 1] = x;
+        }
+        const T rest = sh0[(i * G::HB + by) * G::WR + bxr];
+        const T pp = spp[(i * G::HB + by) * G::WR + bxr];
+        T e;
+        sphi[i * PL + by * SW + (bxr - G::HXR + 1)] = node_phi<P>(rest, mov, pp, e);
+        if (err) err[i] = e;
+      }
+    };
+    // own node (ly = ty + 1, lx = tx + 1; box column tx + HX, row ty + 1)
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = gx < nx && gy < ny;
+    T perr[NP];
+    if (active) {
+      box_phi(tx + G::HXM, tx + G::HXR, ty + 1, perr);
+    } else {
+      phi_global<P, NP>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
+                        (ty + 1) * SW + tx + 1);
+    }
+    constexpr int NRING = SW * SH - BX * BY;
+    if (tid < NRING) {
+      int lx, ly;
+      ring_pos<1>(tid, lx, ly);
+      const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
+      if (rx >= 0 && rx < nx && ry >= 0 && ry < ny)
+        box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, ly, nullptr);
+      else
+        phi_global<P, NP>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
+                          ly * SW + lx);
+    }
+    __syncthreads();
+
+    if (active) {
+      T hreg[NP][9], g[9], pp[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        hreg[i][0] = sh0[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+          T x = to_T(shm[((i * 8 + k - 1) * G::HB + ty + 1) * G::WM + tx + G::HXM]);
+          if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sh_ld);
+          hreg[i][k] = x;
+        }
+        pp[i] = spp[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
+      }
+#pragma unroll
+      for (int k = 1; k < 9; ++k) {
+        T x = to_T(sgm[((k - 1) * BY + ty) * BX + tx]);
+        if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sg_ld);
+        g[k] = x;
+      }
+      const T upx = sup[ty * BX + tx], upy = sup[(BY + ty) * BX + tx];
+      NodeMac<P, NP> m;
+      node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1,
+                                       0, 0, g, m);
+      collide_stream<P, NP, false, WALL>(a, m, hreg, perr, g, pp, upx, upy, gx, gy);
+    }
+    __syncthreads();  // stage j % S and sphi are free again
+    if (tid == 0 && issued < nmine) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(issued);
+      ++issued;
+    }
+  }
+  if (failed_at >= 0) {
+    // Record the timeout, then let the copies still in flight (tiles
+    // failed_at .. issued-1, one per stage) land, with the same bounded wait,
+    // before the CTA's shared memory is released.
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      for (int j = failed_at; j < issued; ++j)
+        mbar_wait(bar + (j % S), (uint32_t)((j / S) & 1));
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -696,6 +987,30 @@ template <int P, int NP, bool NU, bool WALL>
 cudaError_t launch_tile_t(const Consts &c, const Grid &g, int cur, int mode,
                           const Outputs &o, cudaStream_t s) {
   const KArgs<P> a = make_args<P>(c, g, cur, mode, o);
+  if constexpr (P != LBM_FP64 && !NU) {
+    if (mode == MODE_STEP && g.use_tma) {
+      typedef TmaStage<P, NP> St;
+      static int max_ctas = 0;  // per instantiation: resident CTAs on the GPU
+      if (max_ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(
+            tile_kernel_tma<P, NP, WALL>,
+            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)St::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, tile_kernel_tma<P, NP, WALL>, NT, St::SMEM);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        max_ctas = (per_sm > 0 ? per_sm : 1) * sms;
+      }
+      const int ntx = tiles_x(g.nx), ntiles = ntx * tiles_y(g.ny);
+      const int grid = ntiles < max_ctas ? ntiles : max_ctas;
+      tile_kernel_tma<P, NP, WALL><<<grid, dim3(BX, BY), St::SMEM, s>>>(
+          a, *(const TmaMaps *)&g.tma[cur], ntx, ntiles);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid(tiles_x(g.nx), tiles_y(g.ny)), block(BX, BY);
   tile_kernel<P, NP, NU, WALL><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
@@ -723,6 +1038,46 @@ cudaError_t launch_tile_p(const Consts &c, const Grid &g, int cur, int mode,
     case 4: return launch_tile_np<P, 4>(c, g, cur, mode, o, nonunif, wall, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// Tensor maps of the pipelined kernel for both buffers; false if the grid
+// does not meet TMA's alignment rules or an encode fails.
+template <int P>
+bool encode_tma_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  typedef TmaGeom<P> G;
+  if constexpr (P == LBM_FP64) {
+    return false;
+  } else {
+    if (!enc || g.nx % 8 != 0) return false;
+    const int NP = c.NP;
+    auto enc3 = [&](CUtensorMap *m, void *base, size_t es, int planes, int bw,
+                    int bh, int bp) {
+      const CUtensorMapDataType dt =
+          es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+      const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny,
+                                  (cuuint64_t)planes};
+      const cuuint64_t strides[2] = {(cuuint64_t)g.nx * es,
+                                     (cuuint64_t)g.nx * g.ny * es};
+      const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bp};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      return enc(m, dt, 3, base, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int b = 0; b < 2; ++b) {
+      TmaMaps &m = *(TmaMaps *)&g.tma[b];
+      bool ok = enc3(&m.hm, g.hm[b], sizeof(Sm), 8 * NP, G::WM, G::HB, 8 * NP) &&
+                enc3(&m.h0, g.h0[b], sizeof(T), NP, G::WR, G::HB, NP) &&
+                enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HB, NP) &&
+                enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, BY, 8) &&
+                enc3(&m.up, g.u_prev, sizeof(T), 2, BX, BY, 2);
+      if (!ok) return false;
+    }
+    return true;
+  }
 }
 
 template <int P, int NP>
@@ -772,5 +1127,8 @@ cudaError_t launch_init_p(const Consts &c, const Grid &g, int cur,
                                    const double *cin, const double *uin,       \
                                    double p0, bool wall, cudaStream_t s) {     \
     return launch_init_p<P>(c, g, cur, cin, uin, p0, wall, s);                 \
+  }                                                                            \
+  bool encode_tma_##SUFFIX(const Consts &c, Grid &g, EncodeTiledFn enc) {      \
+    return encode_tma_p<P>(c, g, enc);                                         \
   }                                                                            \
   }
