@@ -672,6 +672,16 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 // Halo positions that wrap around the domain (periodic edges, wall ghost
 // rows, ragged tails) are summed from global memory instead.
 // ---------------------------------------------------------------------------
+// Pipeline shape per storage form, chosen by timing the N=5 2048^2 step on
+// GB300 (one CTA per SM either way):
+//  - FP32: 2 stages, u(t-1) staged with the tile, two barriers per tile (the
+//    stage is refilled right after the tile, so the next-but-one tile loads
+//    during a whole tile). A third stage needs 227 KB of shared memory and
+//    leaves ~28 KB of L1; it ran 28% slower, and one barrier per tile with 2
+//    stages 23% slower.
+//  - 16-bit: 3 stages (150 KB), u(t-1) loaded directly, one barrier per tile
+//    (stage j-1 refilled after the phi barrier of tile j), ~3-5% faster than
+//    two barriers; 4 stages (200 KB) ran 5% slower.
 template <int P> struct TmaGeom {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
@@ -680,7 +690,10 @@ template <int P> struct TmaGeom {
   static constexpr int WM = BX + 2 * HXM;           // box widths
   static constexpr int WR = BX + 2 * HXR;
   static constexpr int HB = BY + 2;                 // box height
-  static constexpr int S = sizeof(Sm) == 2 ? 3 : 2; // pipeline stages
+  static constexpr bool WIDE = sizeof(Sm) == 4;     // FP32 storage
+  static constexpr int S = WIDE ? 2 : 3;            // pipeline stages
+  static constexpr bool STAGE_U = WIDE;             // u(t-1) in the stage
+  static constexpr bool TWO_BARRIERS = WIDE;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -734,15 +747,18 @@ template <int P, int NP> struct TmaStage {
   static constexpr size_t H0 = al((size_t)NP * G::HB * G::WR * sizeof(T));
   static constexpr size_t PP = H0;
   static constexpr size_t GM = al((size_t)8 * BY * BX * sizeof(Sm));
-  static constexpr size_t UP = al((size_t)2 * BY * BX * sizeof(T));
+  static constexpr size_t UP = G::STAGE_U ? al((size_t)2 * BY * BX * sizeof(T)) : 0;
   static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
   // bytes the TMA engine writes per stage (full boxes, including fill)
   static constexpr uint32_t TX =
       (uint32_t)((size_t)8 * NP * G::HB * G::WM * sizeof(Sm) +
                  2 * (size_t)NP * G::HB * G::WR * sizeof(T) +
-                 (size_t)8 * BY * BX * sizeof(Sm) + (size_t)2 * BY * BX * sizeof(T));
+                 (size_t)8 * BY * BX * sizeof(Sm) +
+                 (G::STAGE_U ? (size_t)2 * BY * BX * sizeof(T) : 0));
   static constexpr size_t SPHI = al((size_t)NP * (BY + 2) * (BX + 2) * sizeof(T));
-  static constexpr size_t SMEM = G::S * BYTES + SPHI + 64;
+  static constexpr int S = G::S;
+  static constexpr size_t SMEM = S * BYTES + 2 * SPHI + 64;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
 template <int P, int NP, bool WALL>
@@ -753,11 +769,10 @@ __global__ void __launch_bounds__(NT, 1)
   typedef typename Prec<P>::Sm Sm;
   typedef TmaGeom<P> G;
   typedef TmaStage<P, NP> St;
-  constexpr int S = G::S;
+  constexpr int S = St::S;
   constexpr int SW = BX + 2, SH = BY + 2, PL = SW * SH;
   extern __shared__ __align__(128) unsigned char smem[];
-  T *sphi = (T *)(smem + S * St::BYTES);
-  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::SPHI);
+  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + 2 * St::SPHI);
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int nx = a.nx, ny = a.ny;
@@ -773,7 +788,8 @@ __global__ void __launch_bounds__(NT, 1)
     tma_load_3d(st + St::HM, &maps.h0, x0 - G::HXR, y0 - 1, 0, b);
     tma_load_3d(st + St::HM + St::H0, &maps.pp, x0 - G::HXR, y0 - 1, 0, b);
     tma_load_3d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, 0, b);
-    tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0, y0, 0, b);
+    if (G::STAGE_U)
+      tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0, y0, 0, b);
   };
 
   if (tid == 0) {
@@ -788,17 +804,24 @@ __global__ void __launch_bounds__(NT, 1)
   for (int j = 0; j < nmine; ++j) {
     const int t = blockIdx.x + j * gridDim.x;
     const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
+    T *sphi = (T *)(smem + S * St::BYTES + (j & 1) * St::SPHI);
     const unsigned char *st = smem + (j % S) * St::BYTES;
     const Sm *shm = (const Sm *)st;
     const T *sh0 = (const T *)(st + St::HM);
     const T *spp = (const T *)(st + St::HM + St::H0);
     const Sm *sgm = (const Sm *)(st + St::HM + St::H0 + St::PP);
+    // u(t-1) of the own node: from the stage, or straight from global memory
+    // (the load is then in flight while the tile's phi is summed).
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = gx < nx && gy < ny;
+    const size_t qn = (size_t)(active ? gy : 0) * nx + (active ? gx : 0);
     const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
+    const T upx = G::STAGE_U ? T(0) : a.u_prev[qn];
+    const T upy = G::STAGE_U ? T(0) : a.u_prev[a.V + qn];
+    // A thread whose wait gave up still runs the phi sums below (on stale
+    // shared data, harmlessly); the barrier after them makes the decision
+    // to stop the same for the whole CTA.
     const bool ok = mbar_wait(bar + (j % S), (uint32_t)((j / S) & 1));
-    if (__syncthreads_or(!ok)) {
-      failed_at = j;
-      break;
-    }
 
     // phi on the tile and its ring. A position whose node lies inside the
     // array without wrapping reads the staged box; others read global memory.
@@ -820,8 +843,6 @@ __global__ void __launch_bounds__(NT, 1)
       }
     };
     // own node (ly = ty + 1, lx = tx + 1; box column tx + HX, row ty + 1)
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool active = gx < nx && gy < ny;
     T perr[NP];
     if (active) {
       box_phi(tx + G::HXM, tx + G::HXR, ty + 1, perr);
@@ -840,7 +861,19 @@ __global__ void __launch_bounds__(NT, 1)
         phi_global<P, NP>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
                           ly * SW + lx);
     }
-    __syncthreads();
+    // After this barrier every thread is done with tile j - 1. With one
+    // barrier per tile its stage is refilled here with tile j - 1 + S (sphi
+    // is double-buffered, so the stencils of tile j - 1 never race the phi
+    // of tile j); with two, at the end of the tile.
+    if (__syncthreads_or(!ok)) {
+      failed_at = j;
+      break;
+    }
+    if (!G::TWO_BARRIERS && tid == 0 && j > 0 && issued < nmine) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(issued);
+      ++issued;
+    }
 
     if (active) {
       T hreg[NP][9], g[9], pp[NP];
@@ -861,17 +894,21 @@ __global__ void __launch_bounds__(NT, 1)
         if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sg_ld);
         g[k] = x;
       }
-      const T upx = sup[ty * BX + tx], upy = sup[(BY + ty) * BX + tx];
       NodeMac<P, NP> m;
       node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1,
                                        0, 0, g, m);
-      collide_stream<P, NP, false, WALL>(a, m, hreg, perr, g, pp, upx, upy, gx, gy);
+      collide_stream<P, NP, false, WALL>(
+          a, m, hreg, perr, g, pp,
+          G::STAGE_U ? sup[ty * BX + tx] : upx,
+          G::STAGE_U ? sup[(BY + ty) * BX + tx] : upy, gx, gy);
     }
-    __syncthreads();  // stage j % S and sphi are free again
-    if (tid == 0 && issued < nmine) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(issued);
-      ++issued;
+    if (G::TWO_BARRIERS) {
+      __syncthreads();
+      if (tid == 0 && issued < nmine) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(issued);
+        ++issued;
+      }
     }
   }
   if (failed_at >= 0) {
