@@ -132,7 +132,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sel)}
 
 
-def accept_sigma(N):
+def accept_sigma(N=None):
     """sigma draws whose lambda (from the library's host setup) is well
     conditioned: smallest eigenvalue > 1e-3 largest."""
     from paper_1904_12553_gb300 import LbmError, lbm_nphase_derive, workloads as W
@@ -221,6 +221,60 @@ def e2e_run(w, prec, steps):
     return V * steps / t / 1e6, h2d / steps, d2h / steps
 
 
+def batch_run(steps=50, ncases=256):
+    """Batched ensemble (256 seeded static-drop / lens cases, sides 64..512,
+    N = 3..5, FP32): one persistent launch per step under a CUDA graph with
+    the autotuned schedule, against the same cases stepped one by one."""
+    import torch
+    from paper_1904_12553_gb300 import Batch, Solver, workloads as W
+
+    cases = W.ensemble(seed=5, ncases=ncases, accept=accept_sigma(None))
+    nodes = sum(w.V for w in cases)
+    b = Batch([w.params for w in cases])
+    for i, w in enumerate(cases):
+        b.init(i, w.c0, w.u0)
+    b.autotune(3)
+    for i, w in enumerate(cases):
+        b.init(i, w.c0, w.u0)
+    b.step(2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    sched = b.schedule()
+    b.close()
+    solvers = []
+    for w in cases:
+        s = Solver(w.params)
+        s.init(w.c0, w.u0)
+        s.step(1)
+        solvers.append(s)
+    torch.cuda.synchronize()
+    e0.record(solvers[0].stream)
+    for _ in range(steps):
+        for s in solvers:
+            s.step(1)
+    e1.record(solvers[0].stream)
+    torch.cuda.synchronize()
+    ms_1 = e0.elapsed_time(e1)
+    for s in solvers:
+        s.close()
+    return {"cases": ncases, "nodes": nodes, "steps": steps,
+            "batched_mlups": nodes * steps / (ms_b / 1e3) / 1e6,
+            "one_by_one_mlups": nodes * steps / (ms_1 / 1e3) / 1e6,
+            "batched_ms_per_step": ms_b / steps,
+            "one_by_one_ms_per_step": ms_1 / steps,
+            "schedule": {"tile_height": sched["tile_height"],
+                         "schedule": Batch.SCHEDULES[sched["schedule"]],
+                         "ctas": sched["ctas"]},
+            "kernel_launches_per_step": {"batched": 1,
+                                         "one_by_one": ncases}}
+
+
 def cpu_baseline(steps=3):
     """The FP64 oracle on the full workload, timed on this host's cores in a
     fresh process (OpenMP over rows, all cores)."""
@@ -299,6 +353,8 @@ def run_ours(args, dist, rank, world):
                 "mlups": V / (fstep / 1e3) / 1e6, "ms_per_step": fstep,
                 "alg_bytes_per_node": fB, "kernel": fkernel,
                 "hbm_frac": fB * V / (fstep / 1e3) / 1e9 / peak}
+    if not args.quick:
+        forms["batch"] = batch_run()
     e2e_v, h2d, d2h = e2e_run(w, "fp32", args.steps)
     cpu = cpu_baseline() if (world == 1 and not args.quick) else None
     line = {
@@ -316,7 +372,7 @@ def run_ours(args, dist, rank, world):
                      "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind,
                      "alg_bytes_per_node": B,
-                     "traffic": traffic_from_profiles("tile_kernel_fp32_n5_2048")},
+                     "traffic": traffic_from_profiles("tile_kernel_tma_fp32_n5_2048")},
         "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,

@@ -163,6 +163,70 @@ lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
 lbm_status lbm_nphase_diagnostics_static(lbm_nphase_t *h, double *mass,
                                          double *ke, double *umax);
 
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent grids advanced together.
+ *
+ * Cases may differ in size, N, walls and parameters; all use FP32 storage
+ * and equal pure-phase densities (J~ = 0). Each time step of the whole batch
+ * is one persistent kernel launch that walks a list of (case, tile) work
+ * items; steps are replayed from a CUDA graph captured at schedule time.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_nphase_batch_t lbm_nphase_batch_t;
+
+typedef struct {
+  int32_t tile_height; /* 4 or 8 rows of 32 nodes per work item */
+  int32_t schedule;    /* 0: CTA b takes items b, b + ctas, ... of the
+                          cost-ordered list; 1: per-CTA contiguous runs of
+                          equal cost; 2: items taken from an atomic counter */
+  int32_t ctas;        /* persistent CTAs (0: all that are resident) */
+} lbm_nphase_batch_schedule;
+
+/* Workspace for `ncases` grids described by params[0..ncases-1] (0 if a
+ * parameter set is invalid, not FP32, or has unequal densities). */
+size_t lbm_nphase_batch_workspace_bytes(const lbm_nphase_params *params,
+                                        int ncases);
+
+/* Create the batch in caller-owned device memory (256-byte aligned) on the
+ * current device; work is ordered on `cuda_stream`. The initial schedule is
+ * {8, 2, 0}. Errors as lbm_nphase_create. */
+lbm_status lbm_nphase_batch_create(const lbm_nphase_params *params, int ncases,
+                                   void *d_workspace, size_t workspace_bytes,
+                                   void *cuda_stream, lbm_nphase_batch_t **out);
+
+/* Initial state of case `c`, as lbm_nphase_init. Every case must be
+ * initialised before lbm_nphase_batch_step. */
+lbm_status lbm_nphase_batch_init(lbm_nphase_batch_t *b, int c, const double *c0,
+                                 const double *u, double p0);
+
+/* Advance every case by nsteps time steps (asynchronous): one persistent
+ * launch per step, two steps per graph replay. */
+lbm_status lbm_nphase_batch_step(lbm_nphase_batch_t *b, int64_t nsteps);
+
+/* Handle of case `c` (owned by the batch; do not destroy). Use it with
+ * lbm_nphase_moments and lbm_nphase_diagnostics. Stepping it alone with
+ * lbm_nphase_step takes it out of step with the batch (lbm_nphase_batch_step
+ * then returns LBM_ESTATE until the case is re-initialised). */
+lbm_nphase_t *lbm_nphase_batch_case(lbm_nphase_batch_t *b, int c);
+
+/* Time every tile height x schedule (with all resident CTAs) over
+ * 2 * trial_steps steps each and keep the fastest; its time per step goes to
+ * *best_ms_per_step (may be NULL). The trials advance the cases' state by
+ * 12 * (trial_steps + 1) steps: re-initialise afterwards for a clean run. */
+lbm_status lbm_nphase_batch_autotune(lbm_nphase_batch_t *b, int trial_steps,
+                                     double *best_ms_per_step);
+
+/* Set or read the schedule explicitly (rebuilds the work lists and graphs). */
+lbm_status lbm_nphase_batch_set_schedule(lbm_nphase_batch_t *b,
+                                         const lbm_nphase_batch_schedule *s);
+lbm_status lbm_nphase_batch_get_schedule(const lbm_nphase_batch_t *b,
+                                         lbm_nphase_batch_schedule *s);
+
+/* Number of cases. */
+int lbm_nphase_batch_size(const lbm_nphase_batch_t *b);
+
+/* Release the batch and its case handles (not the workspace). NULL ok. */
+lbm_status lbm_nphase_batch_destroy(lbm_nphase_batch_t *b);
+
 /* Number of time steps taken since the last init. */
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
 

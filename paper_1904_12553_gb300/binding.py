@@ -54,6 +54,11 @@ class LbmModel(C.Structure):
     ]
 
 
+class LbmSchedule(C.Structure):
+    _fields_ = [("tile_height", C.c_int32), ("schedule", C.c_int32),
+                ("ctas", C.c_int32)]
+
+
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -89,6 +94,23 @@ def load_library():
         lib.lbm_nphase_steps_taken.argtypes = [vp]
         lib.lbm_nphase_steps_taken.restype = C.c_int64
         lib.lbm_nphase_cuda_error.argtypes = [vp]
+        lib.lbm_nphase_batch_workspace_bytes.argtypes = [pp, C.c_int]
+        lib.lbm_nphase_batch_workspace_bytes.restype = C.c_size_t
+        lib.lbm_nphase_batch_create.argtypes = [pp, C.c_int, vp, C.c_size_t,
+                                                vp, C.POINTER(vp)]
+        lib.lbm_nphase_batch_init.argtypes = [vp, C.c_int, dp, dp, C.c_double]
+        lib.lbm_nphase_batch_step.argtypes = [vp, C.c_int64]
+        lib.lbm_nphase_batch_case.argtypes = [vp, C.c_int]
+        lib.lbm_nphase_batch_case.restype = vp
+        lib.lbm_nphase_batch_autotune.argtypes = [vp, C.c_int,
+                                                  C.POINTER(C.c_double)]
+        lib.lbm_nphase_batch_set_schedule.argtypes = [vp, C.POINTER(LbmSchedule)]
+        lib.lbm_nphase_batch_get_schedule.argtypes = [vp, C.POINTER(LbmSchedule)]
+        lib.lbm_nphase_batch_size.argtypes = [vp]
+        lib.lbm_nphase_batch_destroy.argtypes = [vp]
+        for name in ("create", "init", "step", "autotune", "set_schedule",
+                     "get_schedule", "destroy"):
+            getattr(lib, "lbm_nphase_batch_" + name).restype = C.c_int
         lib.lbm_nphase_uses_pipelined_kernel.argtypes = [vp]
         lib.lbm_nphase_uses_pipelined_kernel.restype = C.c_int
         lib.lbm_nphase_destroy.argtypes = [vp]
@@ -306,3 +328,155 @@ class Solver:
     @property
     def steps_taken(self) -> int:
         return lbm_nphase_steps_taken(self.handle)
+
+
+# ---------------------------------------------------------------------------
+# Batched ensemble
+# ---------------------------------------------------------------------------
+
+def _param_array(params_list):
+    arr = (LbmParams * len(params_list))()
+    for i, p in enumerate(params_list):
+        arr[i] = make_params(p)
+    return arr
+
+
+def lbm_nphase_batch_workspace_bytes(params_list) -> int:
+    return int(load_library().lbm_nphase_batch_workspace_bytes(
+        _param_array(params_list), len(params_list)))
+
+
+def lbm_nphase_batch_create(params_list, workspace_ptr: int, nbytes: int,
+                            stream_ptr: int) -> int:
+    b = C.c_void_p()
+    _check(load_library().lbm_nphase_batch_create(
+        _param_array(params_list), len(params_list), C.c_void_p(workspace_ptr),
+        nbytes, C.c_void_p(stream_ptr), C.byref(b)), "lbm_nphase_batch_create")
+    return b.value
+
+
+def lbm_nphase_batch_init(batch: int, case: int, c_ptr: int, u_ptr,
+                          p0: float = 0.0):
+    _check(load_library().lbm_nphase_batch_init(
+        C.c_void_p(batch), int(case), c_ptr, u_ptr or None, float(p0)),
+        "lbm_nphase_batch_init")
+
+
+def lbm_nphase_batch_step(batch: int, nsteps: int):
+    _check(load_library().lbm_nphase_batch_step(C.c_void_p(batch),
+                                                int(nsteps)),
+           "lbm_nphase_batch_step")
+
+
+def lbm_nphase_batch_case(batch: int, case: int) -> int:
+    return load_library().lbm_nphase_batch_case(C.c_void_p(batch), int(case))
+
+
+def lbm_nphase_batch_autotune(batch: int, trial_steps: int) -> float:
+    ms = C.c_double()
+    _check(load_library().lbm_nphase_batch_autotune(
+        C.c_void_p(batch), int(trial_steps), C.byref(ms)),
+        "lbm_nphase_batch_autotune")
+    return ms.value
+
+
+def lbm_nphase_batch_set_schedule(batch: int, tile_height: int, schedule: int,
+                                  ctas: int = 0):
+    s = LbmSchedule(tile_height, schedule, ctas)
+    _check(load_library().lbm_nphase_batch_set_schedule(C.c_void_p(batch),
+                                                        C.byref(s)),
+           "lbm_nphase_batch_set_schedule")
+
+
+def lbm_nphase_batch_get_schedule(batch: int) -> dict:
+    s = LbmSchedule()
+    _check(load_library().lbm_nphase_batch_get_schedule(C.c_void_p(batch),
+                                                        C.byref(s)),
+           "lbm_nphase_batch_get_schedule")
+    return {"tile_height": s.tile_height, "schedule": s.schedule,
+            "ctas": s.ctas}
+
+
+def lbm_nphase_batch_destroy(batch: int):
+    load_library().lbm_nphase_batch_destroy(C.c_void_p(batch))
+
+
+class Batch:
+    """Many independent grids advanced together (FP32, equal densities)."""
+
+    SCHEDULES = {0: "strided", 1: "cost-balanced lists", 2: "dynamic"}
+
+    def __init__(self, params_list, stream=None, device=None):
+        import torch
+
+        self.torch = torch
+        self.params = [dict(p) for p in params_list]
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        nbytes = lbm_nphase_batch_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise LbmError(1, "lbm_nphase_batch_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8,
+                                     device=self.device)
+        self.handle = lbm_nphase_batch_create(
+            self.params, self.workspace.data_ptr(), nbytes,
+            self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_nphase_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.params)
+
+    def init(self, case: int, c0, u0=None, p0: float = 0.0):
+        t = self.torch
+        p = self.params[case]
+        N, ny, nx = int(p["N"]), int(p["ny"]), int(p["nx"])
+        c = t.as_tensor(np.ascontiguousarray(c0, dtype=np.float64)).to(self.device)
+        assert tuple(c.shape) == (N, ny, nx)
+        u = None
+        if u0 is not None:
+            u = t.as_tensor(np.ascontiguousarray(u0, dtype=np.float64)).to(self.device)
+        lbm_nphase_batch_init(self.handle, case, c.data_ptr(),
+                              None if u is None else u.data_ptr(), p0)
+
+    def step(self, n: int = 1):
+        lbm_nphase_batch_step(self.handle, n)
+
+    def autotune(self, trial_steps: int = 3) -> float:
+        return lbm_nphase_batch_autotune(self.handle, trial_steps)
+
+    def set_schedule(self, tile_height: int, schedule: int, ctas: int = 0):
+        lbm_nphase_batch_set_schedule(self.handle, tile_height, schedule, ctas)
+
+    def schedule(self) -> dict:
+        return lbm_nphase_batch_get_schedule(self.handle)
+
+    def case_handle(self, case: int) -> int:
+        return lbm_nphase_batch_case(self.handle, case)
+
+    def moments(self, case: int) -> dict:
+        t = self.torch
+        p = self.params[case]
+        N, sh = int(p["N"]), (int(p["ny"]), int(p["nx"]))
+        out = {"phi": t.empty((N - 1,) + sh, dtype=t.float64, device=self.device),
+               "c": t.empty((N,) + sh, dtype=t.float64, device=self.device),
+               "u": t.empty((2,) + sh, dtype=t.float64, device=self.device),
+               "p": t.empty(sh, dtype=t.float64, device=self.device),
+               "rho": t.empty(sh, dtype=t.float64, device=self.device)}
+        lbm_nphase_moments(self.case_handle(case), out["phi"].data_ptr(),
+                           out["c"].data_ptr(), out["u"].data_ptr(),
+                           out["p"].data_ptr(), out["rho"].data_ptr())
+        return {k: v.cpu().numpy() for k, v in out.items()}
+
+    def diagnostics(self, case: int):
+        return lbm_nphase_diagnostics(self.case_handle(case),
+                                      int(self.params[case]["N"]))

@@ -1,0 +1,508 @@
+// Batched ensemble: many independent grids (uneven sizes, N = 2..5, walls
+// or periodic) advanced by one persistent launch per time step, replayed from
+// a captured CUDA graph, with the tile height and the CTA-to-tile schedule
+// chosen by measurement (lbm_nphase_batch_autotune).
+//
+// Each case is an ordinary single-grid handle carved from the batch
+// workspace, so init, moments and diagnostics of a case are the single-grid
+// entry points. The batch kernel walks a list of (case, tile) items; for each
+// item it loads the case's kernel arguments into shared memory and runs the
+// same per-node arithmetic as the single-grid kernels (node_macros,
+// collide_stream), for FP32 storage and equal pure-phase densities.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "lbm_kernels.cuh"
+#include "lbm_nphase.h"
+
+namespace lbm {
+
+// Per-case descriptor: kernel arguments for input buffer 0 and 1.
+template <int P> struct BatchCase {
+  KArgs<P> a[2];
+  int np, wall, ntx, nty;
+};
+
+// Ring entry r of a (BX + 2) x (TBY + 2) tile: top row, bottom row, left
+// column, right column.
+template <int TBY>
+__device__ __forceinline__ void ring_pos_1(int r, int &lx, int &ly) {
+  constexpr int SW = BX + 2;
+  if (r < SW) {
+    ly = 0; lx = r;
+  } else if (r < 2 * SW) {
+    ly = TBY + 1; lx = r - SW;
+  } else if (r < 2 * SW + TBY) {
+    ly = 1 + (r - 2 * SW); lx = 0;
+  } else {
+    ly = 1 + (r - 2 * SW - TBY); lx = BX + 1;
+  }
+}
+
+// One time step of one BX x TBY tile of one case (equal densities).
+template <int P, int NP, bool WALL, int TBY>
+__device__ __forceinline__ void tile_step_body(const KArgs<P> &a, int x0, int y0,
+                                               typename Prec<P>::T *sphi) {
+  typedef typename Prec<P>::T T;
+  constexpr int SW = BX + 2, SH = TBY + 2, PL = SW * SH;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int nx = a.nx, ny = a.ny;
+  const size_t V = a.V;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = gx < nx && gy < ny;
+  T hreg[NP][9], perr[NP];
+  {
+    const int sx = wrap(gx, nx), sy = wrap_y<WALL>(gy, ny);
+    const size_t q = (size_t)sy * nx + sx;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      hreg[i][0] = ldg(a.h0_in + (size_t)i * V + q);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) hreg[i][k] = load_hm<P>(a, i, k, q);
+      const T pp = ldg(a.pp_in + (size_t)i * V + q);
+      sphi[i * PL + (ty + 1) * SW + tx + 1] =
+          node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i]);
+    }
+  }
+  constexpr int NRING = SW * SH - BX * TBY;
+  for (int r = tid; r < NRING; r += BX * TBY) {
+    int lx, ly;
+    ring_pos_1<TBY>(r, lx, ly);
+    phi_global<P, NP>(a, wrap(x0 - 1 + lx, nx), wrap_y<WALL>(y0 - 1 + ly, ny),
+                      sphi, PL, ly * SW + lx);
+  }
+  __syncthreads();
+  if (active) {
+    const size_t q = (size_t)gy * nx + gx;
+    T g[9], pp[NP];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) g[k] = load_gm<P>(a, k, q);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) pp[i] = ldg(a.pp_in + (size_t)i * V + q);
+    NodeMac<P, NP> m;
+    node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1, 0,
+                                     0, g, m);
+    collide_stream<P, NP, false, WALL>(a, m, hreg, perr, g, pp, a.u_prev[q],
+                                       a.u_prev[V + q], gx, gy);
+  }
+  __syncthreads();  // sphi is reused by the next item
+}
+
+enum BatchSched { SCHED_STRIDE = 0, SCHED_LISTS = 1, SCHED_DYNAMIC = 2 };
+
+template <int P, int TBY>
+__global__ void __launch_bounds__(BX *TBY)
+    batch_kernel(const BatchCase<P> *__restrict__ cases,
+                 const int2 *__restrict__ items, int nitems,
+                 const int *__restrict__ list_off, const int *__restrict__ list,
+                 int sched, int *counter, int cur) {
+  typedef typename Prec<P>::T T;
+  constexpr int SW = BX + 2, SH = TBY + 2;
+  __shared__ KArgs<P> sa;
+  __shared__ T sphi[4 * SW * SH];
+  __shared__ int s_item, s_np, s_wall, s_ntx;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  int loaded = -1;
+  int k = 0;
+  const int lbeg = sched == SCHED_LISTS ? list_off[blockIdx.x] : 0;
+  const int lend = sched == SCHED_LISTS ? list_off[blockIdx.x + 1] : 0;
+  for (;;) {
+    int item;
+    if (sched == SCHED_DYNAMIC) {
+      if (tid == 0) s_item = atomicAdd(counter, 1);
+      __syncthreads();
+      item = s_item;
+      __syncthreads();
+    } else if (sched == SCHED_LISTS) {
+      item = lbeg + k < lend ? list[lbeg + k] : nitems;
+    } else {
+      item = blockIdx.x + k * gridDim.x;
+    }
+    ++k;
+    if (item >= nitems) break;
+    const int2 it = items[item];
+    if (it.x != loaded) {
+      // Case arguments into shared memory (word copy of a plain struct).
+      const unsigned *src = (const unsigned *)&cases[it.x].a[cur];
+      unsigned *dst = (unsigned *)&sa;
+      for (int w = tid; w < (int)(sizeof(KArgs<P>) / 4); w += BX * TBY) dst[w] = src[w];
+      if (tid == 0) {
+        s_np = cases[it.x].np;
+        s_wall = cases[it.x].wall;
+        s_ntx = cases[it.x].ntx;
+      }
+      __syncthreads();
+      loaded = it.x;
+    }
+    const int x0 = (it.y % s_ntx) * BX, y0 = (it.y / s_ntx) * TBY;
+    switch (s_np * 2 + s_wall) {
+      case 2: tile_step_body<P, 1, false, TBY>(sa, x0, y0, sphi); break;
+      case 3: tile_step_body<P, 1, true, TBY>(sa, x0, y0, sphi); break;
+      case 4: tile_step_body<P, 2, false, TBY>(sa, x0, y0, sphi); break;
+      case 5: tile_step_body<P, 2, true, TBY>(sa, x0, y0, sphi); break;
+      case 6: tile_step_body<P, 3, false, TBY>(sa, x0, y0, sphi); break;
+      case 7: tile_step_body<P, 3, true, TBY>(sa, x0, y0, sphi); break;
+      case 8: tile_step_body<P, 4, false, TBY>(sa, x0, y0, sphi); break;
+      case 9: tile_step_body<P, 4, true, TBY>(sa, x0, y0, sphi); break;
+    }
+  }
+}
+
+}  // namespace lbm
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+using lbm::BatchCase;
+typedef BatchCase<LBM_FP32> Case32;
+
+namespace {
+constexpr int kTileHeights[2] = {4, 8};
+constexpr int kMaxCtas = 4096;  // bound of the per-CTA schedule lists
+size_t align256b(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+struct lbm_nphase_batch_t {
+  int n;
+  std::vector<lbm_nphase_t *> cases;
+  cudaStream_t stream;     // caller's stream
+  cudaStream_t cap;        // private stream for graph capture
+  Case32 *d_cases;         // descriptors (device)
+  int2 *d_items;           // (case, tile) items (device)
+  int *d_list_off, *d_list, *d_counter;
+  size_t items_cap, lists_cap;
+  int nitems;
+  lbm_nphase_batch_schedule sched;
+  int max_ctas[2];         // resident CTAs per tile height
+  cudaGraphExec_t exec[2]; // two steps starting at buffer 0 / 1
+  int cur;
+  int64_t steps;
+  int cuda_err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_nphase_batch_t *b, cudaError_t e) {
+  b->cuda_err = (int)e;
+  return LBM_ECUDA;
+}
+
+size_t case_bytes(const lbm_nphase_params &p) {
+  return align256b(lbm_nphase_workspace_bytes(&p));
+}
+
+size_t tiles_for(const lbm_nphase_params &p, int tby) {
+  return (size_t)lbm::tiles_x(p.nx) * ((p.ny + tby - 1) / tby);
+}
+
+void destroy_graphs(lbm_nphase_batch_t *b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->exec[p]) {
+      cudaGraphExecDestroy(b->exec[p]);
+      b->exec[p] = nullptr;
+    }
+}
+
+cudaError_t launch_once(lbm_nphase_batch_t *b, cudaStream_t s, int cur) {
+  const int ti = b->sched.tile_height == 4 ? 0 : 1;
+  int grid = b->sched.ctas;
+  if (b->sched.schedule == lbm::SCHED_DYNAMIC) {
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (ti == 0)
+    lbm::batch_kernel<LBM_FP32, 4><<<grid, dim3(lbm::BX, 4), 0, s>>>(
+        b->d_cases, b->d_items, b->nitems, b->d_list_off, b->d_list,
+        b->sched.schedule, b->d_counter, cur);
+  else
+    lbm::batch_kernel<LBM_FP32, 8><<<grid, dim3(lbm::BX, 8), 0, s>>>(
+        b->d_cases, b->d_items, b->nitems, b->d_list_off, b->d_list,
+        b->sched.schedule, b->d_counter, cur);
+  return cudaGetLastError();
+}
+
+// Work items and schedules for one tile height and CTA count.
+lbm_status build_schedule(lbm_nphase_batch_t *b, lbm_nphase_batch_schedule s) {
+  const int tby = s.tile_height;
+  const int ti = tby == 4 ? 0 : 1;
+  if (tby != 4 && tby != 8) return LBM_EINVAL;
+  if (s.schedule < 0 || s.schedule > 2) return LBM_EINVAL;
+  if (s.ctas <= 0) s.ctas = b->max_ctas[ti];
+  if (s.ctas > b->max_ctas[ti]) s.ctas = b->max_ctas[ti];
+  // Cases in order of decreasing work (cost of a tile ~ N), tiles of a case
+  // consecutive (neighbouring tiles share halos in L2).
+  std::vector<int> order(b->n);
+  std::iota(order.begin(), order.end(), 0);
+  auto cost = [&](int c) {
+    const lbm_nphase_params &p = b->cases[c]->prm;
+    return (double)tiles_for(p, tby) * p.N;
+  };
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return cost(x) > cost(y); });
+  std::vector<int2> items;
+  std::vector<double> icost;
+  for (int c : order) {
+    const size_t nt = tiles_for(b->cases[c]->prm, tby);
+    for (size_t t = 0; t < nt; ++t) {
+      items.push_back(make_int2(c, (int)t));
+      icost.push_back(b->cases[c]->prm.N);
+    }
+  }
+  if (items.size() > b->items_cap) return LBM_ENOMEM;
+  // Per-CTA lists: the cost-ordered item sequence cut into contiguous runs of
+  // equal total cost (tile cost ~ N), so that a CTA keeps one case's
+  // arguments loaded and neighbouring tiles run on the same CTA.
+  std::vector<int> off(s.ctas + 1, 0), list;
+  {
+    std::vector<std::vector<int>> bins(s.ctas);
+    const double total = std::accumulate(icost.begin(), icost.end(), 0.0);
+    const double share = total / s.ctas;
+    int bin = 0;
+    double acc = 0.0;
+    for (size_t i = 0; i < items.size(); ++i) {
+      if (acc >= share * (bin + 1) && bin + 1 < s.ctas) ++bin;
+      bins[bin].push_back((int)i);
+      acc += icost[i];
+    }
+    for (int k = 0; k < s.ctas; ++k) {
+      off[k + 1] = off[k] + (int)bins[k].size();
+      list.insert(list.end(), bins[k].begin(), bins[k].end());
+    }
+  }
+  cudaError_t e;
+  e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_list_off, off.data(), off.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_list, list.data(), list.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, b->stream);
+  // descriptors: ntx/nty for this tile height
+  std::vector<Case32> desc(b->n);
+  for (int c = 0; c < b->n; ++c) {
+    lbm_nphase_t *h = b->cases[c];
+    const lbm::Outputs none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    desc[c].a[0] = lbm::make_args<LBM_FP32>(h->k, h->g, 0, lbm::MODE_STEP, none);
+    desc[c].a[1] = lbm::make_args<LBM_FP32>(h->k, h->g, 1, lbm::MODE_STEP, none);
+    desc[c].np = h->k.NP;
+    desc[c].wall = h->wall ? 1 : 0;
+    desc[c].ntx = lbm::tiles_x(h->prm.nx);
+    desc[c].nty = (h->prm.ny + tby - 1) / tby;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_cases, desc.data(), desc.size() * sizeof(Case32),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  b->nitems = (int)items.size();
+  b->sched = s;
+  // Two steps (buffer 0 -> 1 -> 0 and 1 -> 0 -> 1) captured as graphs.
+  destroy_graphs(b);
+  for (int p = 0; p < 2; ++p) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, e);
+    cudaError_t e1 = launch_once(b, b->cap, p);
+    cudaError_t e2 = launch_once(b, b->cap, p ^ 1);
+    e = cudaStreamEndCapture(b->cap, &graph);
+    if (e1 != cudaSuccess) e = e1;
+    if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[p], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, e);
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_nphase_batch_workspace_bytes(const lbm_nphase_params *params,
+                                        int ncases) {
+  if (!params || ncases <= 0) return 0;
+  size_t total = 0, items = 0;
+  for (int c = 0; c < ncases; ++c) {
+    const lbm_nphase_params &p = params[c];
+    if (p.precision != LBM_FP32) return 0;
+    lbm_nphase_model m;
+    if (lbm_nphase_derive(&p, &m) != LBM_OK || !m.uniform_density) return 0;
+    total += case_bytes(p);
+    items += tiles_for(p, 4);
+  }
+  total += align256b(ncases * sizeof(Case32));
+  total += align256b(items * sizeof(int2));
+  total += align256b((size_t)(kMaxCtas + 1) * sizeof(int));
+  total += align256b(items * sizeof(int));
+  total += align256b(sizeof(int));
+  return total;
+}
+
+lbm_status lbm_nphase_batch_create(const lbm_nphase_params *params, int ncases,
+                                   void *ws, size_t bytes, void *stream,
+                                   lbm_nphase_batch_t **out) {
+  if (!out || !params || ncases <= 0 || !ws || ((uintptr_t)ws & 255u))
+    return LBM_EINVAL;
+  *out = nullptr;
+  const size_t need = lbm_nphase_batch_workspace_bytes(params, ncases);
+  if (need == 0) return LBM_EINVAL;
+  if (bytes < need) return LBM_ENOMEM;
+  lbm_nphase_batch_t *b = new (std::nothrow) lbm_nphase_batch_t();
+  if (!b) return LBM_ENOMEM;
+  b->n = ncases;
+  b->stream = (cudaStream_t)stream;
+  char *base = (char *)ws;
+  size_t off = 0, items = 0;
+  lbm_status st = LBM_OK;
+  for (int c = 0; c < ncases && st == LBM_OK; ++c) {
+    lbm_nphase_t *h = nullptr;
+    const size_t cb = case_bytes(params[c]);
+    st = lbm_nphase_create(&params[c], base + off, cb, stream, &h);
+    if (st == LBM_OK) b->cases.push_back(h);
+    off += cb;
+    items += tiles_for(params[c], 4);
+  }
+  if (st != LBM_OK) {
+    lbm_nphase_batch_destroy(b);
+    return st;
+  }
+  b->d_cases = (Case32 *)(base + off);
+  off += align256b(ncases * sizeof(Case32));
+  b->d_items = (int2 *)(base + off);
+  b->items_cap = items;
+  off += align256b(items * sizeof(int2));
+  b->d_list_off = (int *)(base + off);
+  off += align256b((size_t)(kMaxCtas + 1) * sizeof(int));
+  b->d_list = (int *)(base + off);
+  off += align256b(items * sizeof(int));
+  b->d_counter = (int *)(base + off);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    lbm_nphase_batch_destroy(b);
+    return LBM_ECUDA;
+  }
+  int dev = 0, sms = 0, per4 = 0, per8 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per4, lbm::batch_kernel<LBM_FP32, 4>, lbm::BX * 4, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per8, lbm::batch_kernel<LBM_FP32, 8>, lbm::BX * 8, 0);
+  b->max_ctas[0] = std::min(std::max(per4, 1) * sms, kMaxCtas);
+  b->max_ctas[1] = std::min(std::max(per8, 1) * sms, kMaxCtas);
+  lbm_nphase_batch_schedule s0 = {8, lbm::SCHED_DYNAMIC, 0};
+  st = build_schedule(b, s0);
+  if (st != LBM_OK) {
+    lbm_nphase_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_batch_init(lbm_nphase_batch_t *b, int c,
+                                 const double *frac, const double *u,
+                                 double p0) {
+  if (!b || c < 0 || c >= b->n) return LBM_EINVAL;
+  return lbm::init_at(b->cases[c], frac, u, p0, b->cur);
+}
+
+lbm_status lbm_nphase_batch_step(lbm_nphase_batch_t *b, int64_t nsteps) {
+  if (!b || nsteps < 0) return LBM_EINVAL;
+  for (lbm_nphase_t *h : b->cases)
+    if (!h->initialized || h->unstable || h->cur != b->cur) return LBM_ESTATE;
+  cudaError_t e = cudaSuccess;
+  int64_t t = 0;
+  for (; t + 2 <= nsteps && e == cudaSuccess; t += 2)
+    e = cudaGraphLaunch(b->exec[b->cur], b->stream);
+  if (e == cudaSuccess && t < nsteps) {
+    e = launch_once(b, b->stream, b->cur);
+    if (e == cudaSuccess) b->cur ^= 1;
+  }
+  if (e != cudaSuccess) return bfail(b, e);
+  for (lbm_nphase_t *h : b->cases) {
+    h->cur = b->cur;
+    h->steps += nsteps;
+  }
+  b->steps += nsteps;
+  return LBM_OK;
+}
+
+lbm_nphase_t *lbm_nphase_batch_case(lbm_nphase_batch_t *b, int c) {
+  if (!b || c < 0 || c >= b->n) return nullptr;
+  return b->cases[c];
+}
+
+lbm_status lbm_nphase_batch_set_schedule(lbm_nphase_batch_t *b,
+                                         const lbm_nphase_batch_schedule *s) {
+  if (!b || !s) return LBM_EINVAL;
+  return build_schedule(b, *s);
+}
+
+lbm_status lbm_nphase_batch_get_schedule(const lbm_nphase_batch_t *b,
+                                         lbm_nphase_batch_schedule *s) {
+  if (!b || !s) return LBM_EINVAL;
+  *s = b->sched;
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_batch_autotune(lbm_nphase_batch_t *b, int trial_steps,
+                                     double *best_ms_per_step) {
+  if (!b || trial_steps < 1) return LBM_EINVAL;
+  for (lbm_nphase_t *h : b->cases)
+    if (!h->initialized) return LBM_ESTATE;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return LBM_ECUDA;
+  lbm_nphase_batch_schedule best = b->sched;
+  float best_ms = 1e30f;
+  lbm_status st = LBM_OK;
+  for (int ti = 0; ti < 2 && st == LBM_OK; ++ti)
+    for (int sc = 0; sc < 3 && st == LBM_OK; ++sc) {
+      lbm_nphase_batch_schedule s = {kTileHeights[ti], sc, 0};
+      st = build_schedule(b, s);
+      if (st != LBM_OK) break;
+      st = lbm_nphase_batch_step(b, 2);  // warm-up
+      if (st != LBM_OK) break;
+      cudaEventRecord(e0, b->stream);
+      st = lbm_nphase_batch_step(b, 2 * trial_steps);
+      cudaEventRecord(e1, b->stream);
+      if (st != LBM_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = LBM_ECUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= (float)(2 * trial_steps);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = b->sched;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  if (best_ms_per_step) *best_ms_per_step = best_ms;
+  return build_schedule(b, best);
+}
+
+int lbm_nphase_batch_size(const lbm_nphase_batch_t *b) { return b ? b->n : 0; }
+
+lbm_status lbm_nphase_batch_destroy(lbm_nphase_batch_t *b) {
+  if (!b) return LBM_OK;
+  destroy_graphs(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (lbm_nphase_t *h : b->cases) lbm_nphase_destroy(h);
+  delete b;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -16,22 +16,6 @@ using lbm::Consts;
 using lbm::Grid;
 using lbm::Outputs;
 
-struct lbm_nphase_t {
-  lbm_nphase_params prm;
-  lbm_nphase_model mdl;
-  Consts k;
-  Grid g;
-  int prec;
-  bool nonunif, wall;
-  cudaStream_t stream;
-  int device;
-  double *stage;  // (N + 2) * V doubles: host <-> device staging
-  int cur;        // buffer holding the state at the current time
-  bool initialized, unstable;
-  int64_t steps;
-  int cuda_err;
-};
-
 namespace {
 
 constexpr double CS2 = 1.0 / 3.0;
@@ -483,7 +467,14 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
 
 lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
                            double p0) {
-  if (!h || !c || !isfinite(p0)) return LBM_EINVAL;
+  return lbm::init_at(h, c, u, p0, 0);
+}
+
+}  // extern "C"
+
+lbm_status lbm::init_at(lbm_nphase_t *h, const double *c, const double *u,
+                        double p0, int cur) {
+  if (!h || !c || !isfinite(p0) || (cur != 0 && cur != 1)) return LBM_EINVAL;
   const size_t V = h->g.V;
   const int N = h->prm.N;
   const double *dc = c, *du = u;
@@ -502,16 +493,18 @@ lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
   }
   e = cudaMemsetAsync(h->g.err, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  e = lbm::launch_init(h->prec, h->k, h->g, 0, dc, du, p0, h->wall, h->stream);
+  e = lbm::launch_init(h->prec, h->k, h->g, cur, dc, du, p0, h->wall, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  h->cur = 0;
+  h->cur = cur;
   h->steps = 0;
   h->initialized = true;
   h->unstable = false;
   return LBM_OK;
 }
+
+extern "C" {
 
 lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps) {
   if (!h || nsteps < 0) return LBM_EINVAL;

@@ -99,3 +99,27 @@ inline int tiles_x(int nx) { return (nx + BX - 1) / BX; }
 inline int tiles_y(int ny) { return (ny + BY - 1) / BY; }
 
 }  // namespace lbm
+
+// One grid's handle (the opaque type of the C ABI).
+struct lbm_nphase_t {
+  lbm_nphase_params prm;
+  lbm_nphase_model mdl;
+  lbm::Consts k;
+  lbm::Grid g;
+  int prec;
+  bool nonunif, wall;
+  cudaStream_t stream;
+  int device;
+  double *stage;  // (N + 2) * V doubles: host <-> device staging
+  int cur;        // buffer holding the state at the current time
+  bool initialized, unstable;
+  int64_t steps;
+  int cuda_err;
+};
+
+namespace lbm {
+// lbm_nphase_init with the start state written into buffer `cur` (0 or 1),
+// so that grids stepped together keep the same buffer parity.
+lbm_status init_at(lbm_nphase_t *h, const double *c, const double *u,
+                   double p0, int cur);
+}  // namespace lbm
