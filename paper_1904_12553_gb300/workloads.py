@@ -164,11 +164,16 @@ def static_drops(nx=128, ny=128, R=20.0, centres=((40, 64), (88, 64)), N=3,
 
 def lens(nx=256, ny=256, R=40.0, s13=0.8e-3, s12=1e-3, s23=None,
          tau=0.8, mobility=0.1, rho=None, precision="fp32", steps=20000,
-         eta=ETA_W4, wall_y=1, N=3) -> Workload:
+         eta=ETA_W4, wall_y=1, N=3, beta=0.0) -> Workload:
     """Liquid lens (Section 4.2, Eq. N35 with the drop as phase 3).
 
     Phases 1 | 2 meet at a horizontal interface at y = ny/2; a drop of phase
     3 of radius R sits on it. Periodic in x, bounce-back walls in y.
+
+    ``beta=0.0`` takes Eq. N36 (sigma_min), so the narrowest interface has
+    the width of W = 4; ``beta="flat"`` fixes beta^2 = 3 sqrt(2) sigma_12 eta
+    from the flat 1|2 interface (the paper's lens runs keep one beta for all
+    tension ratios); a number sets it.
     """
     s23 = s13 if s23 is None else s23
     yc, xc = ny / 2.0, nx / 2.0
@@ -181,8 +186,10 @@ def lens(nx=256, ny=256, R=40.0, s13=0.8e-3, s12=1e-3, s23=None,
     sig[0, 1] = sig[1, 0] = s12
     sig[0, 2] = sig[2, 0] = s13
     sig[1, 2] = sig[2, 1] = s23
+    if beta == "flat":
+        beta = math.sqrt(3.0 * math.sqrt(2.0) * s12 * eta)
     p = base_params(N, nx, ny, sig, rho=rho, tau=tau, mobility=mobility,
-                    precision=precision, eta=eta, wall_y=wall_y)
+                    precision=precision, eta=eta, wall_y=wall_y, beta=beta)
     return Workload(f"lens_{nx}x{ny}_s13_{s13:g}", p, c, None, 0.0, steps)
 
 
