@@ -66,8 +66,10 @@ typedef struct {
                           y = -1/2 and y = ny - 1/2 (Section 4.2). x is
                           always periodic. */
   int32_t precision;   /* lbm_precision */
-  int32_t grad_scheme; /* 0: isotropic central scheme, Eq. N31a (the only
-                          value accepted) */
+  int32_t grad_scheme; /* first derivatives: 0 isotropic central scheme,
+                          Eq. N31a; 1 isotropic mixed scheme, Eq. N40, read
+                          with -zeta(x + 2c_i) (the Laplacian is Eq. N31b
+                          either way). 1 runs on the generic kernel. */
   double rho[LBM_MAX_N];              /* pure-phase densities rho~_k > 0 */
   double sigma[LBM_MAX_N][LBM_MAX_N]; /* pairwise surface tensions sigma_kl
                                          > 0, symmetric; diagonal ignored */

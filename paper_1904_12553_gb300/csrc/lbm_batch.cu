@@ -333,7 +333,9 @@ size_t lbm_nphase_batch_workspace_bytes(const lbm_nphase_params *params,
     const lbm_nphase_params &p = params[c];
     if (p.precision != LBM_FP32) return 0;
     lbm_nphase_model m;
-    if (lbm_nphase_derive(&p, &m) != LBM_OK || !m.uniform_density) return 0;
+    if (lbm_nphase_derive(&p, &m) != LBM_OK || !m.uniform_density ||
+        p.grad_scheme != 0)
+      return 0;
     total += case_bytes(p);
     items += tiles_for(p, 4);
   }

@@ -130,7 +130,7 @@ lbm_status validate(const lbm_nphase_params *p) {
   if ((double)p->nx * (double)p->ny > 17179869184.0) return LBM_EINVAL;
   if (p->wall_y != 0 && p->wall_y != 1) return LBM_EINVAL;
   if (p->precision < LBM_FP64 || p->precision > LBM_MIX_FP16) return LBM_EINVAL;
-  if (p->grad_scheme != 0) return LBM_EINVAL;
+  if (p->grad_scheme != 0 && p->grad_scheme != 1) return LBM_EINVAL;
   for (int k = 0; k < p->N; ++k)
     if (!finite_pos(p->rho[k])) return LBM_EINVAL;
   for (int k = 0; k < p->N; ++k)
@@ -451,8 +451,9 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   g.red = (double *)(base + L.red);
   g.red_out = (double *)(base + L.red_out);
   g.err = (int *)(base + L.err);
+  g.grad_scheme = p->grad_scheme;
   g.use_tma = false;
-  if (tma_allowed() && !h->nonunif) {
+  if (tma_allowed() && !h->nonunif && p->grad_scheme == 0) {
     lbm::EncodeTiledFn enc = tensor_map_encoder();
     switch (h->prec) {
       case LBM_FP32: g.use_tma = lbm::encode_tma_f32(k, g, enc); break;

@@ -64,6 +64,7 @@ struct Grid {
   double *red;      // per-block partial sums of the diagnostics
   double *red_out;  // N + 2 reduced diagnostics
   int *err;         // device error word (1: a bounded wait gave up)
+  int grad_scheme;  // 0: central (Eq. N31a), 1: mixed (Eq. N40)
   bool use_tma;     // pipelined kernel usable for this grid
   TmaMaps tma[2];   // its descriptors, input buffer 0 or 1
 };

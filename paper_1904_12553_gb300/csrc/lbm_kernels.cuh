@@ -291,6 +291,27 @@ __device__ __forceinline__ T laplacian(const T *s, int ly, int lx) {
          ((ne + nw) + (se + sw) - T(4) * c) * T(1.0 / 6.0);
 }
 
+// Isotropic mixed gradient of Eq. N40, read with -zeta(x + 2 c_i): the mean
+// of the central and the second-order upwind directional differences.
+template <typename T, int W>
+__device__ __forceinline__ void gradient_mixed(const T *s, int ly, int lx,
+                                               T &gx, T &gy) {
+  const T c = s[ly * W + lx];
+  T sx = T(0), sy = T(0);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    const int dx = cx_of(k), dy = cy_of(k);
+    const T d = -s[(ly + 2 * dy) * W + lx + 2 * dx] +
+                T(5) * s[(ly + dy) * W + lx + dx] - T(3) * c -
+                s[(ly - dy) * W + lx - dx];
+    const T wd = w_of<T>(k) * d;
+    if (dx != 0) sx += T(dx) * wd;
+    if (dy != 0) sy += T(dy) * wd;
+  }
+  gx = sx * T(0.75);  // 1 / (4 c_s^2)
+  gy = sy * T(0.75);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -316,7 +337,7 @@ template <int P, int NP> struct NodeMac {
 // phi and its stencils from the shared tile (centre ly, lx), C_i (from the
 // shared C tile when densities differ), J~ and grad rho, F, u (Eq. N22_1)
 // and p (Eq. N23). g[1..8] are the node's NS populations.
-template <int P, int NP, bool NU, int SW, int CW>
+template <int P, int NP, bool NU, int SW, int CW, bool G40 = false>
 __device__ __forceinline__ void node_macros(const KArgs<P> &a,
                                             const typename Prec<P>::T *sphi,
                                             int plane, const typename Prec<P>::T *sC,
@@ -330,6 +351,8 @@ __device__ __forceinline__ void node_macros(const KArgs<P> &a,
     for (int i = 0; i < NP; ++i) {
       m.ph[i] = sphi[i * plane + ly * SW + lx];
       stencil<T, SW>(sphi + i * plane, ly, lx, m.gpx[i], m.gpy[i], lp[i]);
+      if constexpr (G40)
+        gradient_mixed<T, SW>(sphi + i * plane, ly, lx, m.gpx[i], m.gpy[i]);
     }
     local_algebra<P, NP>(a, m.ph, m.cc, m.rho, hf);
     if constexpr (NU) {
@@ -350,7 +373,10 @@ __device__ __forceinline__ void node_macros(const KArgs<P> &a,
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       T cgx, cgy;
-      gradient<T, CW>(sC + i * cplane, cly, clx, cgx, cgy);
+      if constexpr (G40)
+        gradient_mixed<T, CW>(sC + i * cplane, cly, clx, cgx, cgy);
+      else
+        gradient<T, CW>(sC + i * cplane, cly, clx, cgx, cgy);
       m.Jx -= a.kmob[i] * cgx;
       m.Jy -= a.kmob[i] * cgy;
       m.grx += a.kap[i] * m.gpx[i];
@@ -524,13 +550,15 @@ __device__ __forceinline__ void phi_global(const KArgs<P> &a, int sx, int sy,
 // time step; MODE_MOMENTS: write the macroscopic fields; MODE_DIAG: per-CTA
 // partial sums of the diagnostics).
 // ---------------------------------------------------------------------------
-template <int P, int NP, bool NU, bool WALL>
+template <int P, int NP, bool NU, bool WALL, bool G40>
 __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   typedef typename Prec<P>::T T;
-  constexpr int R = NU ? 2 : 1;     // phi halo radius
-  constexpr int SW = BX + 2 * R;    // shared tile width
-  constexpr int SH = BY + 2 * R;    // shared tile height
-  constexpr int CW = NU ? BX + 2 : 1, CH = NU ? BY + 2 : 1;
+  constexpr int RG = G40 ? 2 : 1;          // reach of a gradient stencil
+  constexpr int RC = NU ? RG : 0;          // C ring radius (for grad C)
+  constexpr int R = RC + 1 > RG ? RC + 1 : RG;  // phi halo radius
+  constexpr int SW = BX + 2 * R;           // shared tile width
+  constexpr int SH = BY + 2 * R;           // shared tile height
+  constexpr int CW = NU ? BX + 2 * RC : 1, CH = NU ? BY + 2 * RC : 1;
   __shared__ T sphi[NP][SH * SW];
   __shared__ T sC[NP][CH * CW];
 
@@ -567,7 +595,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   }
   __syncthreads();
 
-  // 3. Unequal densities: C_i on the tile and a ring of radius 1, then wall
+  // 3. Unequal densities: C_i on the tile and a ring of radius RC, then wall
   //    ghost rows of C repeat the adjacent fluid row.
   if constexpr (NU) {
     for (int r = tid; r < CW * CH; r += NT) {
@@ -575,8 +603,8 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
       T ph[NP], lp[NP], cc[NP + 1], rho, hf[NP];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        ph[i] = sphi[i][(cy + 1) * SW + cxl + 1];
-        lp[i] = laplacian<T, SW>(sphi[i], cy + 1, cxl + 1);
+        ph[i] = sphi[i][(cy + R - RC) * SW + cxl + R - RC];
+        lp[i] = laplacian<T, SW>(sphi[i], cy + R - RC, cxl + R - RC);
       }
       local_algebra<P, NP>(a, ph, cc, rho, hf);
 #pragma unroll
@@ -591,10 +619,10 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
     if constexpr (WALL) {
       for (int r = tid; r < CW * CH; r += NT) {
         const int cy = r / CW, cxl = r % CW;
-        const int yg = y0 - 1 + cy;
+        const int yg = y0 - RC + cy;
         if (yg < 0 || yg >= ny) {
           const int ys = yg < 0 ? 0 : ny - 1;
-          const int cys = ys - y0 + 1;
+          const int cys = ys - y0 + RC;
 #pragma unroll
           for (int i = 0; i < NP; ++i) sC[i][r] = sC[i][cys * CW + cxl];
         }
@@ -609,8 +637,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 #pragma unroll
   for (int k = 1; k < 9; ++k) g[k] = active ? load_gm<P>(a, k, q) : T(0);
   NodeMac<P, NP> m;
-  node_macros<P, NP, NU, SW, CW>(a, &sphi[0][0], SH * SW, &sC[0][0], CH * CW,
-                                 ty + R, tx + R, ty + 1, tx + 1, g, m);
+  node_macros<P, NP, NU, SW, CW, G40>(a, &sphi[0][0], SH * SW, &sC[0][0],
+                                      CH * CW, ty + R, tx + R, ty + RC,
+                                      tx + RC, g, m);
 
   if (a.mode == MODE_MOMENTS) {
     if (!active) return;
@@ -1025,7 +1054,7 @@ cudaError_t launch_tile_t(const Consts &c, const Grid &g, int cur, int mode,
                           const Outputs &o, cudaStream_t s) {
   const KArgs<P> a = make_args<P>(c, g, cur, mode, o);
   if constexpr (P != LBM_FP64 && !NU) {
-    if (mode == MODE_STEP && g.use_tma) {
+    if (mode == MODE_STEP && g.use_tma && g.grad_scheme == 0) {
       typedef TmaStage<P, NP> St;
       static int max_ctas = 0;  // per instantiation: resident CTAs on the GPU
       if (max_ctas == 0) {
@@ -1049,7 +1078,10 @@ cudaError_t launch_tile_t(const Consts &c, const Grid &g, int cur, int mode,
     }
   }
   dim3 grid(tiles_x(g.nx), tiles_y(g.ny)), block(BX, BY);
-  tile_kernel<P, NP, NU, WALL><<<grid, block, 0, s>>>(a);
+  if (g.grad_scheme == 1)
+    tile_kernel<P, NP, NU, WALL, true><<<grid, block, 0, s>>>(a);
+  else
+    tile_kernel<P, NP, NU, WALL, false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -193,6 +193,27 @@ def lens(nx=256, ny=256, R=40.0, s13=0.8e-3, s12=1e-3, s23=None,
     return Workload(f"lens_{nx}x{ny}_s13_{s13:g}", p, c, None, 0.0, steps)
 
 
+def puddle(g, nx=400, ny=200, R=30.0, sigma=0.01, rho=(3.0, 1.0, 6.0),
+           tau=0.8, mobility=0.1, precision="fp32", steps=200000,
+           eta=ETA_W4) -> Workload:
+    """Lens under gravity (Section 4.2, Eq. N37): a drop of phase 1
+    (density 3) on the interface between phase 2 above (density 1) and phase
+    3 below (density 6), body force G = (0, -rho g), walls in y, periodic in
+    x, equal sigma. For large g the drop flattens into a puddle whose
+    thickness the paper compares with de Gennes' asymptote (Eq. N37)."""
+    N = 3
+    yc, xc = ny / 2.0, nx / 2.0
+    c = np.zeros((N, ny, nx))
+    c[0] = drop(nx, ny, xc, yc, R, eta, px=True, py=False)
+    _, y = _grid(nx, ny)
+    c[1] = np.maximum(_step(y - yc, eta) - c[0], 0.0)
+    c[2] = 1.0 - c[0] - c[1]
+    p = base_params(N, nx, ny, sigma, rho=list(rho), tau=tau,
+                    mobility=mobility, precision=precision, eta=eta, wall_y=1,
+                    gravity=(0.0, -g))
+    return Workload(f"puddle_g{g:g}_{nx}x{ny}", p, c, None, 0.0, steps)
+
+
 def _place(rng, nx, ny, radii, gap, tries=20000):
     """Seeded non-overlapping centres with min-image spacing r_a+r_b+gap."""
     cs = []

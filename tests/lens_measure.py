@@ -68,3 +68,17 @@ def angles(d, h_up, h_down):
 def neumann_symmetric(s12, s):
     """Cap angle of a symmetric lens (sigma_13 = sigma_23 = s), Eq. N32."""
     return math.degrees(math.acos(s12 / (2 * s)))
+
+
+def de_gennes_thickness(g, spread, rho1, rho2, rho3, upper=True):
+    """Asymptotic thickness of a puddle of fluid 1 floating between fluid 2
+    above and fluid 3 below, with spread = s12 + s13 - s23 > 0 (Eq. N37).
+
+    Balancing the hydrostatic pressure across a vertical cut through the
+    puddle against the three tensions (Archimedes fixes the immersed part)
+    gives H^2 = 2 spread (rho3 - rho2) / (g (rho1 - rho2)(rho3 - rho1)).
+    Eq. N37 as printed is its rho2 -> 0 limit (upper=False)."""
+    if not upper:
+        rho2 = 0.0
+    return math.sqrt(2.0 * spread * (rho3 - rho2) /
+                     (g * (rho1 - rho2) * (rho3 - rho1)))

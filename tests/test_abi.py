@@ -92,7 +92,7 @@ def _bad(**kw):
     dict(N=1), dict(N=6), dict(nx=0), dict(ny=-3), dict(tau_g=0.5),
     dict(tau=[0.8, 0.4]), dict(mobility=[0.1, 0.0]), dict(eta=0.0),
     dict(rho=[1.0, -1.0, 1.0]), dict(precision=7), dict(wall_y=2),
-    dict(grad_scheme=1),
+    dict(grad_scheme=2),
     dict(sigma=[[0, 1e-3, 1e-3], [2e-3, 0, 1e-3], [1e-3, 1e-3, 0]]),
     dict(sigma=[[0, 1e-3, 0], [1e-3, 0, 1e-3], [0, 1e-3, 0]]),
 ])

@@ -275,13 +275,14 @@ def test_surface_tension_integral():
 # Whole-step properties
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("wall", [0, 1])
-def test_mass_conservation(wall):
+def test_mass_conservation(wall, scheme):
     """Sum_x phi_i (hence sum_x c_k) is invariant: collision keeps sum_k h_k
     (sum h^eq = phi, sum R = 0) and streaming / bounce-back only moves
-    populations."""
+    populations -- with either gradient scheme (Eq. N31a or Eq. N40)."""
     w = W.random_smooth(7, 4, 23, 17, rho=[3.0, 1.0, 2.0, 5.0], wall_y=wall,
-                        amp_u=0.02, gravity=(0.0, -1e-5))
+                        amp_u=0.02, gravity=(0.0, -1e-5), grad_scheme=scheme)
     s = oracle.OracleSim(w.params)
     s.init(w.c0, w.u0)
     m0 = s.moments()["phi"].sum((1, 2))

@@ -110,6 +110,51 @@ def test_fp64_short_runs(N, nx, ny, wall, nonunif):
         compare(g, o, 1e-12, 1e-13, 1e-12)
 
 
+# The mixed gradient scheme of Eq. N40 (radius 2; radius-3 phi halo with
+# unequal densities).
+G40 = [(N, nx, ny, wall, nonunif)
+       for N in (2, 3, 5)
+       for (nx, ny) in ((37, 29), (70, 45), (6, 5))
+       for wall in (0, 1)
+       for nonunif in (False, True)]
+
+
+@pytest.mark.parametrize("N,nx,ny,wall,nonunif", G40)
+def test_fp64_mixed_gradient_short_runs(N, nx, ny, wall, nonunif):
+    seed = 3000 + 1000 * N + 10 * nx + ny + 7 * wall + int(nonunif)
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.5, 8.0, N) if nonunif else None
+    w = W.random_smooth(seed, N, nx, ny, rho=rho, wall_y=wall, amp_u=0.02,
+                        gravity=(1e-5, -2e-5) if nonunif else (0.0, 0.0),
+                        grad_scheme=1,
+                        sigma=W.sample_sigma(rng, N, accept=_accept(N, rho)))
+    for steps in (1, 20):
+        compare(gpu_run(w, steps), oracle_run(w, steps), 1e-12, 1e-13, 1e-12)
+
+
+def test_five_phases_mixed_gradient_fp64_1000_steps():
+    """Five phases with the paper's choice for N = 5 (Eq. N40) and its
+    densities 6:4:1:2:3, reduced to 96x96."""
+    w = W.droplets_interfaces(seed=4, n=96, ndrops=4, precision="fp64",
+                              accept=_accept(5))
+    w.params["grad_scheme"] = 1
+    w.params["rho"] = [6.0, 4.0, 1.0, 2.0, 3.0]
+    w.params["sigma"] = W.base_params(5, 4, 4, 1e-3)["sigma"]
+    w.params["mobility"] = [0.01] * 4
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_mixed_gradient_reduced_precision(prec):
+    """Eq. N40 in the FP32 / 16-bit storage forms (generic kernel) against
+    the FP64 oracle after 1000 steps."""
+    w = W.static_drops()
+    w.params["grad_scheme"] = 1
+    o = oracle_run(w, 1000)
+    g = gpu_run(w, 1000, prec=prec, expect_pipelined=False)
+    assert maxdiff(g["phi"], o["phi"]) <= 1e-3
+
+
 # ---------------------------------------------------------------------------
 # The accuracy target: FP64, 1000 steps.
 # ---------------------------------------------------------------------------

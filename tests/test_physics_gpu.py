@@ -125,3 +125,78 @@ def test_thin_lens_and_ordering(lens_results):
     assert abs(t1 / want - 1) <= 0.15 and abs(t2 / want - 1) <= 0.15
     th = [sum(lens_results[s][0]) / 2 for s in (0.6e-3, 0.8e-3, 1.0e-3)]
     assert th[0] < th[1] < th[2]
+
+
+def _thickness(c_drop):
+    """Largest vertical extent of the c_drop > 1/2 region (linear
+    interpolation of the contour at both ends) over the columns."""
+    ny, nx = c_drop.shape
+    best = 0.0
+    for x in range(nx):
+        col = c_drop[:, x]
+        idx = np.where(col > 0.5)[0]
+        if len(idx) == 0 or idx.min() == 0 or idx.max() == ny - 1:
+            continue
+        lo, hi = idx.min(), idx.max()
+        y0 = lo - 1 + (0.5 - col[lo - 1]) / (col[lo] - col[lo - 1])
+        y1 = hi + (0.5 - col[hi]) / (col[hi + 1] - col[hi])
+        best = max(best, y1 - y0)
+    return best
+
+
+@pytest.fixture(scope="module")
+def puddles():
+    """Equilibrated drops under gravity (densities 3:1:6, equal sigma =
+    0.01, R = 30, 400x200, FP32), run in chunks of 2e4 steps until the
+    thickness moves less than 0.02 per chunk (at most 4e5 steps)."""
+    from paper_1904_12553_gb300 import Solver
+    out = {}
+    for g in (2e-5, 5e-5, 1e-4):
+        w = W.puddle(g)
+        s = Solver(w.params)
+        s.init(w.c0)
+        prev, steps = None, 0
+        while steps < 400_000:
+            s.step(20000)
+            steps += 20000
+            H = _thickness(s.moments()["c"][0])
+            if prev is not None and abs(H - prev) < 0.02:
+                break
+            prev = H
+        mass, ke, umax = s.diagnostics()
+        s.close()
+        Hd = LM.de_gennes_thickness(g, 0.01, 3.0, 1.0, 6.0)
+        Hp = LM.de_gennes_thickness(g, 0.01, 3.0, 1.0, 6.0, upper=False)
+        print(f"\npuddle g={g:g}: steps={steps} H={H:.2f} balance={Hd:.2f} "
+              f"rel={H / Hd - 1:+.3f} (Eq. N37 as printed {Hp:.2f}, "
+              f"rel={H / Hp - 1:+.3f}) umax={umax:.2e}")
+        out[g] = (H, Hd)
+    return out
+
+
+def test_puddle_thickness_de_gennes(puddles):
+    """Puddle thickness against de Gennes' balance including the upper
+    fluid's density (densities 3:1:6): within 10% for g = 2e-5 .. 1e-4
+    (-2.2%, +1.1%, +7.4% measured when written; the thinnest puddle, 13
+    nodes, carries the interface-width error), falling with g."""
+    hs = [puddles[g][0] for g in (2e-5, 5e-5, 1e-4)]
+    assert hs[0] > hs[1] > hs[2]
+    for g in (2e-5, 5e-5, 1e-4):
+        H, Hd = puddles[g]
+        assert abs(H / Hd - 1) <= 0.10, (g, H, Hd)
+
+
+def test_puddle_geometry_parity_fp64():
+    """Gravity, unequal densities (J~, grad rho) and walls on the puddle
+    geometry, reduced to 100x50 with R = 10: FP64 GPU against the oracle
+    after 1000 steps."""
+    from paper_1904_12553_gb300 import Solver
+    w = W.puddle(1e-4, nx=100, ny=50, R=10.0, precision="fp64")
+    s = Solver(w.params)
+    s.init(w.c0)
+    s.step(1000)
+    g = s.moments()
+    s.close()
+    o = oracle.run(w.params, w.c0, steps=1000)
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-10
+    assert np.abs(g["u"] - o["u"]).max() <= 1e-12
