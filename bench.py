@@ -146,6 +146,20 @@ def accept_sigma(N=None):
     return ok
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """Largest value over all ranks (the slowest replica sets the time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, nodes: int, steps: int, ms_max: float) -> float:
+    """Whole-job MLUPS of `world` replicas of a grid of `nodes` nodes, each
+    taking `steps` steps, timed by the slowest replica."""
+    return world * nodes * steps / (ms_max / 1e3) / 1e6
+
+
 def make_workload(prec="fp32", n=2048, accept=None):
     from paper_1904_12553_gb300 import workloads as W
     return W.droplets_interfaces(seed=SEED, n=n, precision=prec,
@@ -182,9 +196,7 @@ def time_form(w, prec, steps, warmup, dist=None):
     ms = e0.elapsed_time(e1)
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     mass, ke, _ = s.diagnostics()
     kernel = "pipelined (TMA)" if s.pipelined else "generic tile"
     s.close()
@@ -326,7 +338,7 @@ def run_ours(args, dist, rank, world):
         sampler.mark(wa, wb)
     clocks = sampler.stop() if sampler else None
     ms_step = ms / args.steps
-    value = world * V * args.steps / (ms / 1e3) / 1e6
+    value = replica_value(world, V, args.steps, ms)
     if rank != 0:
         return
     peak, peak_kind = peaks()

@@ -127,8 +127,10 @@ lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
 /* Advance nsteps >= 0 time steps (asynchronous on the handle's stream). Each
  * step is one fused kernel: zeroth moments (Eq. N28), chemical potentials
  * (Eqs. N17, N18, N31), forces, u and p (Eqs. N22_1, N23), both
- * collisions (Eqs. 24, N24) and streaming. Errors: LBM_ESTATE before init or
- * after LBM_EUNSTABLE, LBM_ECUDA. */
+ * collisions (Eqs. 24, N24) and streaming. From nsteps >= 4 on, pairs of
+ * steps are replayed from a CUDA graph captured on the handle's first such
+ * call (on a private stream; call it outside any capture of your own).
+ * Errors: LBM_ESTATE before init or after LBM_EUNSTABLE, LBM_ECUDA. */
 lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps);
 
 /* Macroscopic fields at the current time: phi[N-1][ny][nx], c[N][ny][nx],
@@ -228,6 +230,17 @@ int lbm_nphase_batch_size(const lbm_nphase_batch_t *b);
 
 /* Release the batch and its case handles (not the workspace). NULL ok. */
 lbm_status lbm_nphase_batch_destroy(lbm_nphase_batch_t *b);
+
+/* Checkpoint / resume. The state at the current time (distributions,
+ * phi(t-1), u(t-1) and a 64-byte header with N, nx, ny, precision and the
+ * step count) as one blob of lbm_nphase_state_bytes() bytes, in host or
+ * device memory. lbm_nphase_set_state accepts a blob of a handle with the
+ * same N, grid and precision (else LBM_EINVAL) and leaves the handle
+ * initialised at that state; continuing from it reproduces the uninterrupted
+ * run bit for bit. Both synchronise. Not part of the paper. */
+size_t lbm_nphase_state_bytes(const lbm_nphase_t *h);
+lbm_status lbm_nphase_get_state(lbm_nphase_t *h, void *dst, size_t bytes);
+lbm_status lbm_nphase_set_state(lbm_nphase_t *h, const void *src, size_t bytes);
 
 /* Number of time steps taken since the last init. */
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);

@@ -111,6 +111,12 @@ def load_library():
         for name in ("create", "init", "step", "autotune", "set_schedule",
                      "get_schedule", "destroy"):
             getattr(lib, "lbm_nphase_batch_" + name).restype = C.c_int
+        lib.lbm_nphase_state_bytes.argtypes = [vp]
+        lib.lbm_nphase_state_bytes.restype = C.c_size_t
+        lib.lbm_nphase_get_state.argtypes = [vp, vp, C.c_size_t]
+        lib.lbm_nphase_get_state.restype = C.c_int
+        lib.lbm_nphase_set_state.argtypes = [vp, vp, C.c_size_t]
+        lib.lbm_nphase_set_state.restype = C.c_int
         lib.lbm_nphase_uses_pipelined_kernel.argtypes = [vp]
         lib.lbm_nphase_uses_pipelined_kernel.restype = C.c_int
         lib.lbm_nphase_destroy.argtypes = [vp]
@@ -236,6 +242,22 @@ def lbm_nphase_steps_taken(handle: int) -> int:
     return int(load_library().lbm_nphase_steps_taken(C.c_void_p(handle)))
 
 
+def lbm_nphase_state_bytes(handle: int) -> int:
+    return int(load_library().lbm_nphase_state_bytes(C.c_void_p(handle)))
+
+
+def lbm_nphase_get_state(handle: int, dst_ptr: int, nbytes: int):
+    _check(load_library().lbm_nphase_get_state(C.c_void_p(handle),
+                                               C.c_void_p(dst_ptr), nbytes),
+           "lbm_nphase_get_state")
+
+
+def lbm_nphase_set_state(handle: int, src_ptr: int, nbytes: int):
+    _check(load_library().lbm_nphase_set_state(C.c_void_p(handle),
+                                               C.c_void_p(src_ptr), nbytes),
+           "lbm_nphase_set_state")
+
+
 def lbm_nphase_uses_pipelined_kernel(handle: int) -> bool:
     return bool(load_library().lbm_nphase_uses_pipelined_kernel(
         C.c_void_p(handle)))
@@ -320,6 +342,18 @@ class Solver:
 
     def diagnostics(self):
         return lbm_nphase_diagnostics(self.handle, self.N)
+
+    def get_state(self, device: bool = False):
+        """The current state as a uint8 tensor (host, or device)."""
+        t = self.torch
+        n = lbm_nphase_state_bytes(self.handle)
+        buf = t.empty(n, dtype=t.uint8,
+                      device=self.device if device else "cpu")
+        lbm_nphase_get_state(self.handle, buf.data_ptr(), n)
+        return buf
+
+    def set_state(self, blob):
+        lbm_nphase_set_state(self.handle, blob.data_ptr(), blob.numel())
 
     @property
     def pipelined(self) -> bool:

@@ -507,18 +507,162 @@ lbm_status lbm::init_at(lbm_nphase_t *h, const double *c, const double *u,
 
 extern "C" {
 
+static cudaError_t step_once(lbm_nphase_t *h, cudaStream_t s, int cur) {
+  const Outputs none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  return lbm::launch_tile(h->prec, h->k, h->g, cur, lbm::MODE_STEP, none,
+                          h->nonunif, h->wall, s);
+}
+
+// Two steps (buffer p -> p^1 -> p) captured as a graph, for p = 0 and 1.
+static cudaError_t build_step_graphs(lbm_nphase_t *h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->cap) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t e1 = step_once(h, h->cap, p);
+    cudaError_t e2 = step_once(h, h->cap, p ^ 1);
+    e = cudaStreamEndCapture(h->cap, &graph);
+    if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+    if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[p], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  return e;
+}
+
 lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps) {
   if (!h || nsteps < 0) return LBM_EINVAL;
   if (!h->initialized || h->unstable) return LBM_ESTATE;
-  const Outputs none = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  for (int64_t t = 0; t < nsteps; ++t) {
-    cudaError_t e = lbm::launch_tile(h->prec, h->k, h->g, h->cur,
-                                     lbm::MODE_STEP, none, h->nonunif, h->wall,
-                                     h->stream);
+  int64_t t = 0;
+  if (nsteps >= 4 && !h->gexec[0]) {
+    // one step launched directly first: the launchers' one-time setup
+    // (shared-memory attributes, occupancy) then runs outside the capture
+    cudaError_t e = step_once(h, h->stream, h->cur);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->cur ^= 1;
+    ++h->steps;
+    ++t;
+    e = build_step_graphs(h);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  if (h->gexec[0])
+    for (; t + 2 <= nsteps; t += 2) {
+      cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      h->steps += 2;
+    }
+  for (; t < nsteps; ++t) {
+    cudaError_t e = step_once(h, h->stream, h->cur);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->cur ^= 1;
     ++h->steps;
   }
+  return LBM_OK;
+}
+
+// --------------------------------------------------------------------------
+// Checkpoint / resume: the state at the current time as one blob.
+// --------------------------------------------------------------------------
+namespace {
+struct StateHeader {
+  char magic[8];  // "LBMNPHS1"
+  int32_t N, nx, ny, precision, wall_y, grad_scheme;
+  int64_t steps;
+  uint64_t payload;  // bytes after the header
+  uint8_t pad[16];
+};
+static_assert(sizeof(StateHeader) == 64, "state header");
+
+struct Part {
+  void *dev;
+  size_t bytes;
+};
+
+int state_parts(const lbm_nphase_t *h, Part out[5]) {
+  const size_t V = h->g.V;
+  const int n = h->prm.N - 1;
+  const size_t sT = h->prec == LBM_FP64 ? 8 : 4;
+  const size_t sS = h->prec == LBM_FP64 ? 8 : (h->prec == LBM_FP32 ? 4 : 2);
+  const int c = h->cur;
+  out[0] = {h->g.h0[c], n * V * sT};
+  out[1] = {h->g.hm[c], n * 8 * V * sS};
+  out[2] = {h->g.gm[c], 8 * V * sS};
+  out[3] = {h->g.phi_prev[c], n * V * sT};
+  out[4] = {h->g.u_prev, 2 * V * sT};
+  return 5;
+}
+}  // namespace
+
+size_t lbm_nphase_state_bytes(const lbm_nphase_t *h) {
+  if (!h) return 0;
+  Part parts[5];
+  size_t b = sizeof(StateHeader);
+  for (int i = 0; i < state_parts(h, parts); ++i) b += parts[i].bytes;
+  return b;
+}
+
+lbm_status lbm_nphase_get_state(lbm_nphase_t *h, void *dst, size_t bytes) {
+  if (!h || !dst) return LBM_EINVAL;
+  if (!h->initialized) return LBM_ESTATE;
+  if (bytes < lbm_nphase_state_bytes(h)) return LBM_ENOMEM;
+  StateHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "LBMNPHS1", 8);
+  hd.N = h->prm.N;
+  hd.nx = h->prm.nx;
+  hd.ny = h->prm.ny;
+  hd.precision = h->prm.precision;
+  hd.wall_y = h->prm.wall_y;
+  hd.grad_scheme = h->prm.grad_scheme;
+  hd.steps = h->steps;
+  hd.payload = lbm_nphase_state_bytes(h) - sizeof(hd);
+  const bool dev = is_device_ptr(dst);
+  cudaError_t e = cudaMemcpyAsync(dst, &hd, sizeof(hd),
+                                  dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                                  h->stream);
+  Part parts[5];
+  char *p = (char *)dst + sizeof(hd);
+  for (int i = 0; i < state_parts(h, parts) && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(p, parts[i].dev, parts[i].bytes,
+                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream);
+    p += parts[i].bytes;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return LBM_OK;
+}
+
+lbm_status lbm_nphase_set_state(lbm_nphase_t *h, const void *src, size_t bytes) {
+  if (!h || !src) return LBM_EINVAL;
+  if (bytes < lbm_nphase_state_bytes(h)) return LBM_EINVAL;
+  const bool dev = is_device_ptr(src);
+  StateHeader hd;
+  cudaError_t e = cudaMemcpy(&hd, src, sizeof(hd),
+                             dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (memcmp(hd.magic, "LBMNPHS1", 8) != 0 || hd.N != h->prm.N ||
+      hd.nx != h->prm.nx || hd.ny != h->prm.ny ||
+      hd.precision != h->prm.precision ||
+      hd.payload != lbm_nphase_state_bytes(h) - sizeof(hd))
+    return LBM_EINVAL;
+  h->cur = 0;
+  Part parts[5];
+  const char *p = (const char *)src + sizeof(hd);
+  for (int i = 0; i < state_parts(h, parts) && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(parts[i].dev, p, parts[i].bytes,
+                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        h->stream);
+    p += parts[i].bytes;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->g.err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->steps = hd.steps;
+  h->initialized = true;
+  h->unstable = false;
   return LBM_OK;
 }
 
@@ -611,6 +755,10 @@ int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h) { return h ? h->steps : 0;
 int lbm_nphase_cuda_error(const lbm_nphase_t *h) { return h ? h->cuda_err : 0; }
 
 lbm_status lbm_nphase_destroy(lbm_nphase_t *h) {
+  if (!h) return LBM_OK;
+  for (int p = 0; p < 2; ++p)
+    if (h->gexec[p]) cudaGraphExecDestroy(h->gexec[p]);
+  if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
   return LBM_OK;
 }

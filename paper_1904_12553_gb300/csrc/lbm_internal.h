@@ -116,6 +116,8 @@ struct lbm_nphase_t {
   bool initialized, unstable;
   int64_t steps;
   int cuda_err;
+  cudaStream_t cap;            // private stream for graph capture
+  cudaGraphExec_t gexec[2];    // two steps starting at buffer 0 / 1
 };
 
 namespace lbm {
