@@ -67,7 +67,7 @@ __device__ __forceinline__ void tile_step_body(const KArgs<P> &a, int x0, int y0
       for (int k = 1; k < 9; ++k) hreg[i][k] = load_hm<P>(a, i, k, q);
       const T pp = ldg(a.pp_in + (size_t)i * V + q);
       sphi[i * PL + (ty + 1) * SW + tx + 1] =
-          node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i]);
+          node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i], a.sh_ld);
     }
   }
   constexpr int NRING = SW * SH - BX * TBY;

@@ -170,22 +170,17 @@ KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
 
 template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
-// Moving population k (1..8) of phase i at node q, in T.
+// Moving population k (1..8) of phase i, or NS population k, at node q in
+// stored units: the value itself (FP64, FP32) or s f_k / w_k (16-bit forms).
 template <int P>
 __device__ __forceinline__ typename Prec<P>::T load_hm(const KArgs<P> &a, int i,
                                                        int k, size_t q) {
-  typedef typename Prec<P>::T T;
-  T v = to_T(ldg(a.hm_in + ((size_t)(i * 8 + k - 1)) * a.V + q));
-  if constexpr (Prec<P>::MIX) v = __fmul_rn(v, w_of<T>(k) * a.sh_ld);
-  return v;
+  return to_T(ldg(a.hm_in + ((size_t)(i * 8 + k - 1)) * a.V + q));
 }
 template <int P>
 __device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
                                                        size_t q) {
-  typedef typename Prec<P>::T T;
-  T v = to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
-  if constexpr (Prec<P>::MIX) v = __fmul_rn(v, w_of<T>(k) * a.sg_ld);
-  return v;
+  return to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
 }
 
 // Order parameter of one node from its stored values. FP64: sum of the nine
@@ -194,11 +189,17 @@ __device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
 template <int P>
 __device__ __forceinline__ typename Prec<P>::T node_phi(
     typename Prec<P>::T rest, const typename Prec<P>::T *mov,
-    typename Prec<P>::T pp, typename Prec<P>::T &err) {
+    typename Prec<P>::T pp, typename Prec<P>::T &err,
+    typename Prec<P>::T sh_ld) {
   typedef typename Prec<P>::T T;
   T small = rest;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) small = __fadd_rn_T(small, mov[k]);
+  for (int k = 0; k < 8; ++k) {
+    if constexpr (Prec<P>::MIX)  // mov in stored units s h_k / w_k
+      small = __fmaf_rn(w_of<T>(k + 1) * sh_ld, mov[k], small);
+    else
+      small = __fadd_rn_T(small, mov[k]);
+  }
   if constexpr (P == LBM_FP64) {
     err = T(0);
     return small;
@@ -336,7 +337,7 @@ template <int P, int NP> struct NodeMac {
 
 // phi and its stencils from the shared tile (centre ly, lx), C_i (from the
 // shared C tile when densities differ), J~ and grad rho, F, u (Eq. N22_1)
-// and p (Eq. N23). g[1..8] are the node's NS populations.
+// and p (Eq. N23). g[1..8] are the node's NS populations in stored units.
 template <int P, int NP, bool NU, int SW, int CW, bool G40 = false>
 __device__ __forceinline__ void node_macros(const KArgs<P> &a,
                                             const typename Prec<P>::T *sphi,
@@ -393,9 +394,11 @@ __device__ __forceinline__ void node_macros(const KArgs<P> &a,
   T mx = T(0), my = T(0), sg = T(0);
 #pragma unroll
   for (int k = 1; k < 9; ++k) {
-    mx += T(cx_of(k)) * g[k];
-    my += T(cy_of(k)) * g[k];
-    sg += g[k];
+    T gk = g[k];  // stored units -> g_k
+    if constexpr (Prec<P>::MIX) gk *= w_of<T>(k) * a.sg_ld;
+    mx += T(cx_of(k)) * gk;
+    my += T(cy_of(k)) * gk;
+    sg += gk;
   }
   const T rinv = T(1) / m.rho;
   m.ux = (mx + T(0.5) * m.Fx) * rinv;
@@ -407,8 +410,9 @@ __device__ __forceinline__ void node_macros(const KArgs<P> &a,
 }
 
 // Collisions and push streaming of one node (steps a7-a10). hreg[i][0] is
-// h_0 (FP64) or d_0 (other forms), hreg[i][1..8] the moving populations,
-// perr the rounding error of phi, pp phi_i(t-1), up u(t-1).
+// h_0 (FP64) or d_0 (other forms), hreg[i][1..8] the moving populations and
+// g[1..8] the NS populations (both in stored units), perr the rounding error
+// of phi, pp phi_i(t-1), up u(t-1).
 template <int P, int NP, bool NU, bool WALL>
 __device__ __forceinline__ void collide_stream(
     const KArgs<P> &a, const NodeMac<P, NP> &m,
@@ -437,61 +441,71 @@ __device__ __forceinline__ void collide_stream(
     }
     dst[k] = (size_t)dy * nx + dx;
   }
-  const T ux = m.ux, uy = m.uy, uu = m.uu, ugr = m.ugr, rho = m.rho;
+  constexpr bool MIX = Prec<P>::MIX;
+  const T ux = m.ux, uy = m.uy, uu = m.uu, rho = m.rho;
   const T Fx = m.Fx, Fy = m.Fy, pr = m.pr;
 
-  // NS collision (Eq. 24) with g^eq (Eq. 25) and G_k (Eq. N20_1).
+  // NS collision (Eq. 24) with g^eq (Eq. 25) and G_k (Eq. N20_1), folded:
+  //   g*_k = (1 - 1/tau_g) g_k + w_k t_k,
+  //   t_k = A0 + C1 c.F + c.u (B1 + B2 c.u + D1 c.F [+ E1 c.grad(rho) + E2 c.J~]),
+  // A0 = (3p - 3/2 rho |u|^2)/tau_g - (1 - 1/(2 tau_g))(3 u.F + 3/2 J~.u/(tau_g - 1/2)).
+  // The u.grad(rho) term of G_k cancels against the trace part of its
+  // (c c - c_s^2 I) contraction. 16-bit forms update s g_k / w_k directly.
+  const T tg = a.tg_inv, ff = a.ffac;
   const T uF = ux * Fx + uy * Fy;
   const T Ju = (m.Jx * ux + m.Jy * uy) * a.jfac;
+  const T A0 = tg * (T(3) * pr - T(1.5) * rho * uu) - ff * (T(3) * uF + T(1.5) * Ju);
+  const T B1 = T(3) * tg * rho, B2 = T(4.5) * tg * rho;
+  const T C1 = T(3) * ff, D1 = T(9) * ff;
+  const T E1 = T(3) * ff, E2 = T(4.5) * ff * a.jfac;
+  const T keep_g = T(1) - tg;
 #pragma unroll
   for (int k = 1; k < 9; ++k) {
     const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
-    const T wk = w_of<T>(k);
     const T cu = cxk * ux + cyk * uy;
     const T cF = cxk * Fx + cyk * Fy;
-    const T geq = wk * (T(3) * pr + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-    // (c c - c_s^2 I) : T / (2 c_s^4) with T = uF + Fu + c_s^2 (u grad rho +
-    // grad rho u) + J~u / (tau_g - 1/2)
-    T QT = T(2) * cu * cF - T(2.0 / 3.0) * uF;
-    if constexpr (NU) {
-      const T cr = cxk * m.grx + cyk * m.gry;
-      const T cJ = cxk * m.Jx + cyk * m.Jy;
-      QT += T(2.0 / 3.0) * cu * cr - T(2.0 / 9.0) * ugr + cJ * cu * a.jfac -
-            T(1.0 / 3.0) * Ju;
-    }
-    const T Gk = wk * (ugr + T(3) * cF + T(4.5) * QT);
-    const T gs = g[k] - (g[k] - geq) * a.tg_inv + a.ffac * Gk;
+    T inner = B1 + B2 * cu + D1 * cF;
+    if constexpr (NU)
+      inner += E1 * (cxk * m.grx + cyk * m.gry) + E2 * (cxk * m.Jx + cyk * m.Jy);
+    const T t = A0 + C1 * cF + cu * inner;
     const int kk = dk[k];
-    if constexpr (Prec<P>::MIX)
+    if constexpr (MIX)
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] =
-          to_S<typename Prec<P>::Sm>(gs * (a.sg_st / w_of<T>(kk)));
+          to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
     else
-      a.gm_out[(size_t)(kk - 1) * V + dst[k]] = gs;
+      a.gm_out[(size_t)(kk - 1) * V + dst[k]] = keep_g * g[k] + w_of<T>(k) * t;
   }
 
-  // CH collisions (Eq. N24) with h^eq (Eq. N25) and R_k (Eqs. N26, N27).
+  // CH collisions (Eq. N24) with h^eq (Eq. N25) and R_k (Eqs. N26, N27),
+  // folded: h*_k = (1 - 1/tau_i) h_k + w_k (alpha + c.beta), alpha =
+  // a_i C_i / tau_i, beta = 3 (phi u / tau_i + (1 - 1/(2 tau_i)) d(phi u)).
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     const T ph = m.ph[i];
-    const T dpx = ph * ux - pp[i] * upx, dpy = ph * uy - pp[i] * upy;
-    const T aC = a.a[i] * m.Cv[i];
     const T ti = a.tau_inv[i];
-    const T sr = a.src[i] * T(3);
+    const T aC = a.a[i] * m.Cv[i];
+    const T dpx = ph * ux - pp[i] * upx, dpy = ph * uy - pp[i] * upy;
+    T al = ti * aC;
+    T bx = T(3) * (ti * ph * ux + a.src[i] * dpx);
+    T by = T(3) * (ti * ph * uy + a.src[i] * dpy);
+    if constexpr (MIX) {  // stored units s h_k / w_k
+      al *= a.sh_st;
+      bx *= a.sh_st;
+      by *= a.sh_st;
+    }
+    const T keep = T(1) - ti;
     T moving_sum = T(0);
 #pragma unroll
     for (int k = 1; k < 9; ++k) {
-      const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
-      const T wk = w_of<T>(k);
-      const T heq = wk * (aC + T(3) * ph * (cxk * ux + cyk * uy));
-      const T Rk = sr * wk * (cxk * dpx + cyk * dpy);
-      const T hs = hreg[i][k] - (hreg[i][k] - heq) * ti + Rk;
+      const T t = al + T(cx_of(k)) * bx + T(cy_of(k)) * by;
       const int kk = dk[k];
-      if constexpr (Prec<P>::MIX) {
-        // 16-bit storage of h_k / w_k, decoded back for the mass balance.
-        const auto sv = to_S<typename Prec<P>::Sm>(hs * (a.sh_st / w_of<T>(kk)));
+      if constexpr (MIX) {
+        const auto sv = to_S<typename Prec<P>::Sm>(keep * hreg[i][k] + t);
         a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = sv;
-        moving_sum = __fadd_rn(moving_sum, __fmul_rn(to_T(sv), w_of<T>(kk) * a.sh_ld));
+        // the mass balance uses the value as stored
+        moving_sum = __fmaf_rn(w_of<T>(kk) * a.sh_ld, to_T(sv), moving_sum);
       } else {
+        const T hs = keep * hreg[i][k] + w_of<T>(k) * t;
         a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = hs;
         moving_sum = __fadd_rn_T(moving_sum, hs);
       }
@@ -499,7 +513,7 @@ __device__ __forceinline__ void collide_stream(
     T rest;
     if constexpr (P == LBM_FP64) {
       const T heq0 = ph + (w_of<T>(0) - T(1)) * aC;
-      rest = hreg[i][0] - (hreg[i][0] - heq0) * ti;
+      rest = keep * hreg[i][0] + ti * heq0;
     } else {
       // h*_0 = (phi + perr) - sum_{k>=1} h*_k (collision conserves sum_k h_k),
       // stored relative to phi: d*_0 = perr - sum_{k>=1} h*_k.
@@ -541,7 +555,8 @@ __device__ __forceinline__ void phi_global(const KArgs<P> &a, int sx, int sy,
 #pragma unroll
     for (int k = 1; k < 9; ++k) mov[k - 1] = load_hm<P>(a, i, k, q);
     const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * a.V + q);
-    out[i * plane + idx] = node_phi<P>(ldg(a.h0_in + (size_t)i * a.V + q), mov, pp, err);
+    out[i * plane + idx] =
+        node_phi<P>(ldg(a.h0_in + (size_t)i * a.V + q), mov, pp, err, a.sh_ld);
   }
 }
 
@@ -582,7 +597,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
       for (int k = 1; k < 9; ++k) hreg[i][k] = load_hm<P>(a, i, k, q);
       const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * V + q);
       sphi[i][(ty + R) * SW + tx + R] =
-          node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i]);
+          node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i], a.sh_ld);
     }
   }
   // 2. Halo ring.
@@ -702,15 +717,16 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 // rows, ragged tails) are summed from global memory instead.
 // ---------------------------------------------------------------------------
 // Pipeline shape per storage form, chosen by timing the N=5 2048^2 step on
-// GB300 (one CTA per SM either way):
-//  - FP32: 2 stages, u(t-1) staged with the tile, two barriers per tile (the
-//    stage is refilled right after the tile, so the next-but-one tile loads
-//    during a whole tile). A third stage needs 227 KB of shared memory and
-//    leaves ~28 KB of L1; it ran 28% slower, and one barrier per tile with 2
-//    stages 23% slower.
-//  - 16-bit: 3 stages (150 KB), u(t-1) loaded directly, one barrier per tile
-//    (stage j-1 refilled after the phi barrier of tile j), ~3-5% faster than
-//    two barriers; 4 stages (200 KB) ran 5% slower.
+// GB300:
+//  - FP32: 2 stages (160 KB, one CTA per SM), u(t-1) staged with the tile,
+//    two barriers per tile (the stage is refilled right after the tile, so
+//    the next-but-one tile loads during a whole tile). A third stage needs
+//    227 KB and leaves ~28 KB of L1: 28% slower; one barrier per tile: 23%
+//    slower; one stage with two CTAs per SM: 15% slower.
+//  - 16-bit: 2 stages (106 KB, two CTAs per SM at <= 128 registers), u(t-1)
+//    loaded directly, one barrier per tile (stage j-1 refilled after the phi
+//    barrier of tile j, phi tile double-buffered). 3 stages with one CTA per
+//    SM: 6% slower; 4 stages: 12% slower.
 template <int P> struct TmaGeom {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
@@ -720,7 +736,7 @@ template <int P> struct TmaGeom {
   static constexpr int WR = BX + 2 * HXR;
   static constexpr int HB = BY + 2;                 // box height
   static constexpr bool WIDE = sizeof(Sm) == 4;     // FP32 storage
-  static constexpr int S = WIDE ? 2 : 3;            // pipeline stages
+  static constexpr int S = 2;                       // pipeline stages
   static constexpr bool STAGE_U = WIDE;             // u(t-1) in the stage
   static constexpr bool TWO_BARRIERS = WIDE;
 };
@@ -859,15 +875,13 @@ __global__ void __launch_bounds__(NT, 1)
       for (int i = 0; i < NP; ++i) {
         T mov[8];
 #pragma unroll
-        for (int k = 1; k < 9; ++k) {
-          T x = to_T(shm[((i * 8 + k - 1) * G::HB + by) * G::WM + bxm]);
-          if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sh_ld);
-          mov[k - 1] = x;
-        }
+        for (int k = 1; k < 9; ++k)
+          mov[k - 1] = to_T(shm[((i * 8 + k - 1) * G::HB + by) * G::WM + bxm]);
         const T rest = sh0[(i * G::HB + by) * G::WR + bxr];
         const T pp = spp[(i * G::HB + by) * G::WR + bxr];
         T e;
-        sphi[i * PL + by * SW + (bxr - G::HXR + 1)] = node_phi<P>(rest, mov, pp, e);
+        sphi[i * PL + by * SW + (bxr - G::HXR + 1)] =
+            node_phi<P>(rest, mov, pp, e, a.sh_ld);
         if (err) err[i] = e;
       }
     };
@@ -910,19 +924,12 @@ __global__ void __launch_bounds__(NT, 1)
       for (int i = 0; i < NP; ++i) {
         hreg[i][0] = sh0[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
 #pragma unroll
-        for (int k = 1; k < 9; ++k) {
-          T x = to_T(shm[((i * 8 + k - 1) * G::HB + ty + 1) * G::WM + tx + G::HXM]);
-          if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sh_ld);
-          hreg[i][k] = x;
-        }
+        for (int k = 1; k < 9; ++k)
+          hreg[i][k] = to_T(shm[((i * 8 + k - 1) * G::HB + ty + 1) * G::WM + tx + G::HXM]);
         pp[i] = spp[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
       }
 #pragma unroll
-      for (int k = 1; k < 9; ++k) {
-        T x = to_T(sgm[((k - 1) * BY + ty) * BX + tx]);
-        if constexpr (Prec<P>::MIX) x = __fmul_rn(x, w_of<T>(k) * a.sg_ld);
-        g[k] = x;
-      }
+      for (int k = 1; k < 9; ++k) g[k] = to_T(sgm[((k - 1) * BY + ty) * BX + tx]);
       NodeMac<P, NP> m;
       node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1,
                                        0, 0, g, m);
