@@ -214,6 +214,50 @@ def puddle(g, nx=400, ny=200, R=30.0, sigma=0.01, rho=(3.0, 1.0, 6.0),
     return Workload(f"puddle_g{g:g}_{nx}x{ny}", p, c, None, 0.0, steps)
 
 
+def paper_four_phase(s13=0.01, precision="fp64", g=1e-5, eta=ETA_W4):
+    """Droplet and bubble under gravity, four phases (Section 5.1):
+    NY x NX = 320 x 200, walls in y; phase 1 drop (D = 60) at (160, 280) in
+    phase 3 (upper half), phase 2 bubble at (160, 40) in phase 4 (lower
+    half); densities 6:1:3:2; sigma_13 = s13, the other pairs 0.01;
+    tau = 0.8, m = 0.1, beta = sqrt(0.06); G = (0, -rho g)."""
+    N, nx, ny, R = 4, 200, 320, 30.0
+    c = np.zeros((N, ny, nx))
+    c[0] = drop(nx, ny, 160.0, 280.0, R, eta, px=True, py=False)
+    c[1] = drop(nx, ny, 160.0, 40.0, R, eta, px=True, py=False)
+    _, y = _grid(nx, ny)
+    c[2] = _step(y - ny / 2.0, eta) * (1.0 - c[0])
+    c[3] = 1.0 - c[0] - c[1] - c[2]
+    sig = np.full((N, N), 0.01)
+    np.fill_diagonal(sig, 0.0)
+    sig[0, 2] = sig[2, 0] = s13
+    p = base_params(N, nx, ny, sig, rho=[6.0, 1.0, 3.0, 2.0], tau=0.8,
+                    mobility=0.1, precision=precision, eta=eta, wall_y=1,
+                    gravity=(0.0, -g), beta=math.sqrt(0.06))
+    return Workload(f"paper_four_phase_s13_{s13:g}", p, c, None, 0.0, 30000)
+
+
+def paper_five_phase(rho=(6.0, 4.0, 1.0, 2.0, 3.0), precision="fp64", g=1e-5,
+                     eta=ETA_W4, grad_scheme=1):
+    """Droplets and interfaces, five phases (Section 5.2): 320 x 200, walls
+    in y; drops of phases 1, 2 (R = 30) at (60, 280), (140, 280) in phase 4
+    (upper), bubble of phase 3 at (100, 40) in phase 5 (lower); equal sigma
+    = 0.01, tau = 0.8, m = 0.1, beta = sqrt(0.06), G = (0, -rho g), the
+    mixed gradient scheme of Eq. N40."""
+    N, nx, ny, R = 5, 200, 320, 30.0
+    c = np.zeros((N, ny, nx))
+    c[0] = drop(nx, ny, 60.0, 280.0, R, eta, px=True, py=False)
+    c[1] = drop(nx, ny, 140.0, 280.0, R, eta, px=True, py=False)
+    c[2] = drop(nx, ny, 100.0, 40.0, R, eta, px=True, py=False)
+    _, y = _grid(nx, ny)
+    c[4] = (1.0 - _step(y - ny / 2.0, eta)) * (1.0 - c[2])
+    c[3] = 1.0 - c[0] - c[1] - c[2] - c[4]
+    p = base_params(N, nx, ny, 0.01, rho=list(rho), tau=0.8, mobility=0.1,
+                    precision=precision, eta=eta, wall_y=1,
+                    gravity=(0.0, -g), beta=math.sqrt(0.06),
+                    grad_scheme=grad_scheme)
+    return Workload("paper_five_phase", p, c, None, 0.0, 30000)
+
+
 def _place(rng, nx, ny, radii, gap, tries=20000):
     """Seeded non-overlapping centres with min-image spacing r_a+r_b+gap."""
     cs = []

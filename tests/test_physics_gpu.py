@@ -200,3 +200,70 @@ def test_puddle_geometry_parity_fp64():
     o = oracle.run(w.params, w.c0, steps=1000)
     assert np.abs(g["phi"] - o["phi"]).max() <= 1e-10
     assert np.abs(g["u"] - o["u"]).max() <= 1e-12
+
+
+def _centroid_y(c):
+    y = np.arange(c.shape[0])[:, None]
+    return float((c * y).sum() / c.sum())
+
+
+@pytest.mark.parametrize("case", ["four", "five"])
+def test_paper_applications_parity_fp64(case):
+    """The paper's 320 x 200 application cases (Sections 5.1, 5.2), full
+    size, FP64 GPU against the oracle after 300 steps."""
+    from paper_1904_12553_gb300 import Solver
+    w = W.paper_four_phase() if case == "four" else W.paper_five_phase()
+    s = Solver(w.params)
+    s.init(w.c0)
+    s.step(300)
+    g = s.moments()
+    s.close()
+    o = oracle.run(w.params, w.c0, steps=300)
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-11
+    assert np.abs(g["u"] - o["u"]).max() <= 1e-13
+
+
+def test_paper_four_phase_motion():
+    """Section 5.1 to t = 12.25 (t = t_l / sqrt(D / g), D = 60): the drop of
+    phase 1 (density 6 in phase 3 of density 3) falls, the bubble of phase 2
+    (1 in 2) rises; per-phase mass is conserved."""
+    from paper_1904_12553_gb300 import Solver
+    w = W.paper_four_phase(precision="fp64")
+    steps = int(12.25 * math.sqrt(60 / 1e-5))
+    s = Solver(w.params)
+    s.init(w.c0)
+    m0, _, _ = s.diagnostics()
+    s.step(steps)
+    m1, ke, umax = s.diagnostics()
+    c = s.moments()["c"]
+    s.close()
+    y1, y2 = _centroid_y(c[0]), _centroid_y(c[1])
+    print(f"\nfour phases, {steps} steps: drop y 280 -> {y1:.1f}, bubble y 40 "
+          f"-> {y2:.1f}, umax={umax:.3e}, mass drift "
+          f"{np.abs(m1 / m0 - 1).max():.1e}")
+    assert np.abs(m1 / m0 - 1).max() <= 1e-10
+    assert y1 < 280 - 20 and y2 > 40 + 20
+    assert math.isfinite(ke)
+
+
+def test_paper_five_phase_motion():
+    """Section 5.2 (Eq. N40) to t = 6: the drops of phases 1 and 2 (densities
+    6, 4 in phase 4 of density 2) fall, phase 1 faster; the bubble of phase
+    3 (1 in 3) rises; per-phase mass is conserved."""
+    from paper_1904_12553_gb300 import Solver
+    w = W.paper_five_phase(precision="fp64")
+    steps = int(6.0 * math.sqrt(60 / 1e-5))
+    s = Solver(w.params)
+    s.init(w.c0)
+    m0, _, _ = s.diagnostics()
+    s.step(steps)
+    m1, ke, umax = s.diagnostics()
+    c = s.moments()["c"]
+    s.close()
+    y1, y2, y3 = (_centroid_y(c[k]) for k in range(3))
+    print(f"\nfive phases, {steps} steps: drops y 280 -> {y1:.1f}, {y2:.1f}; "
+          f"bubble y 40 -> {y3:.1f}; umax={umax:.3e}, mass drift "
+          f"{np.abs(m1 / m0 - 1).max():.1e}")
+    assert np.abs(m1 / m0 - 1).max() <= 1e-10
+    assert y1 < y2 < 280 and y3 > 40
+    assert math.isfinite(ke)
