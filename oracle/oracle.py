@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRC3 = os.path.join(_HERE, "lbm_oracle3d.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liblbm_oracle.so")
 _lock = threading.Lock()
@@ -41,15 +42,28 @@ class OrcParams(C.Structure):
     ]
 
 
+class O3Params(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+        ("nz", C.c_int32), ("wall_y", C.c_int32), ("pad_", C.c_int32),
+        ("rho_t", C.c_double * MAXN),
+        ("sigma", (C.c_double * MAXN) * MAXN),
+        ("eta", C.c_double), ("beta", C.c_double), ("tau_g", C.c_double),
+        ("tau", C.c_double * (MAXN - 1)), ("mob", C.c_double * (MAXN - 1)),
+        ("grav", C.c_double * 3), ("rho0", C.c_double),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, no FP contraction, OpenMP rows)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_SRC3))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -90,6 +104,20 @@ def _load():
         lib.orc_source.argtypes = [C.c_double] * 7 + [dp]
         lib.orc_sizeof_params.restype = C.c_int
         assert lib.orc_sizeof_params() == C.sizeof(OrcParams)
+        p3 = C.POINTER(O3Params)
+        lib.o3_create.argtypes = [p3]
+        lib.o3_create.restype = C.c_void_p
+        lib.o3_destroy.argtypes = [C.c_void_p]
+        lib.o3_init.argtypes = [C.c_void_p, dp, dp, C.c_double]
+        lib.o3_step.argtypes = [C.c_void_p, C.c_long]
+        lib.o3_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
+        lib.o3_stencils.argtypes = [C.c_void_p, dp, dp, dp]
+        lib.o3_geq.argtypes = [C.c_double] * 3 + [dp, dp]
+        lib.o3_force_dist.argtypes = [C.c_double, dp, dp, dp, dp, dp]
+        lib.o3_heq.argtypes = [C.c_double] * 3 + [dp, dp]
+        lib.o3_source.argtypes = [C.c_double, C.c_double, dp, C.c_double, dp, dp]
+        lib.o3_sizeof_params.restype = C.c_int
+        assert lib.o3_sizeof_params() == C.sizeof(O3Params)
         _lib = lib
         return lib
 
@@ -277,6 +305,119 @@ class OracleSim:
 def run(params: dict, c0, u0=None, p0: float = 0.0, steps: int = 0) -> dict:
     """Convenience: init, advance ``steps`` and return the moments."""
     s = OracleSim(params)
+    s.init(c0, u0, p0)
+    s.step(steps)
+    m = s.moments()
+    s.close()
+    return m
+
+
+# ---------------------------------------------------------------------------
+# D3Q15 (three dimensions)
+# ---------------------------------------------------------------------------
+
+def make_params3(p: dict) -> O3Params:
+    N = int(p["N"])
+    o = O3Params()
+    o.N, o.nx, o.ny, o.nz = N, int(p["nx"]), int(p["ny"]), int(p["nz"])
+    o.wall_y = int(p.get("wall_y", 0))
+    for k in range(N):
+        o.rho_t[k] = float(p["rho"][k])
+        for l in range(N):
+            o.sigma[k][l] = float(p["sigma"][k][l])
+    o.eta, o.beta, o.tau_g = float(p["eta"]), float(p.get("beta", 0.0)), float(p["tau_g"])
+    for i in range(N - 1):
+        o.tau[i] = float(p["tau"][i])
+        o.mob[i] = float(p["mobility"][i])
+    g = list(p.get("gravity", (0.0, 0.0))) + [0.0] * 3
+    o.grav[0], o.grav[1], o.grav[2] = float(g[0]), float(g[1]), float(g[2])
+    o.rho0 = float(p.get("rho0", 1.0))
+    return o
+
+
+def _v3(v):
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    assert a.shape == (3,)
+    return a
+
+
+def geq3(rho0, pr, rho, u) -> np.ndarray:
+    out = np.zeros(15)
+    _load().o3_geq(rho0, pr, rho, _dp(_v3(u)), _dp(out))
+    return out
+
+
+def force_dist3(tau_g, u, F, grad_rho, J) -> np.ndarray:
+    out = np.zeros(15)
+    _load().o3_force_dist(tau_g, _dp(_v3(u)), _dp(_v3(F)), _dp(_v3(grad_rho)),
+                          _dp(_v3(J)), _dp(out))
+    return out
+
+
+def heq3(a_i, phi, Ci, u) -> np.ndarray:
+    out = np.zeros(15)
+    _load().o3_heq(a_i, phi, Ci, _dp(_v3(u)), _dp(out))
+    return out
+
+
+def source3(tau_i, phi, u, phi_prev, u_prev) -> np.ndarray:
+    out = np.zeros(15)
+    _load().o3_source(tau_i, phi, _dp(_v3(u)), phi_prev, _dp(_v3(u_prev)),
+                      _dp(out))
+    return out
+
+
+class OracleSim3D:
+    """D3Q15 oracle simulation; arrays are [field][z][y][x], u has 3 parts."""
+
+    def __init__(self, params: dict):
+        self.lib = _load()
+        self._p = make_params3(params)
+        self.N = self._p.N
+        self.shape = (self._p.nz, self._p.ny, self._p.nx)
+        self.h = self.lib.o3_create(C.byref(self._p))
+        if not self.h:
+            raise ValueError("oracle rejected the parameters")
+
+    def close(self):
+        if self.h:
+            self.lib.o3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, c0, u0=None, p0: float = 0.0):
+        c0 = np.ascontiguousarray(c0, dtype=np.float64)
+        assert c0.shape == (self.N,) + self.shape
+        if u0 is not None:
+            u0 = np.ascontiguousarray(u0, dtype=np.float64)
+            assert u0.shape == (3,) + self.shape
+        self.lib.o3_init(self.h, _dp(c0), _dp(u0), float(p0))
+
+    def step(self, n: int = 1):
+        self.lib.o3_step(self.h, int(n))
+
+    def moments(self) -> dict:
+        sh = self.shape
+        out = {"phi": np.zeros((self.N - 1,) + sh), "c": np.zeros((self.N,) + sh),
+               "u": np.zeros((3,) + sh), "p": np.zeros(sh), "rho": np.zeros(sh)}
+        self.lib.o3_moments(self.h, *[_dp(out[k]) for k in ("phi", "c", "u", "p", "rho")])
+        return out
+
+    def stencils(self, z):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        grad = np.zeros((3,) + self.shape)
+        lap = np.zeros(self.shape)
+        self.lib.o3_stencils(self.h, _dp(z), _dp(grad), _dp(lap))
+        return grad, lap
+
+
+def run3(params: dict, c0, u0=None, p0: float = 0.0, steps: int = 0) -> dict:
+    s = OracleSim3D(params)
     s.init(c0, u0, p0)
     s.step(steps)
     m = s.moments()

@@ -449,3 +449,83 @@ def random_smooth(seed, N, nx, ny, rho=None, sigma=None, wall_y=0,
                     tau_g=taus[0], mobility=mobs, precision=precision,
                     wall_y=wall_y, gravity=gravity, grad_scheme=grad_scheme)
     return Workload(f"random_N{N}_{nx}x{ny}_s{seed}", p, c, u, 0.0, 0, seed)
+
+
+# --------------------------------------------------------------------------
+# Three dimensions (D3Q15)
+# --------------------------------------------------------------------------
+
+def _grid3(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64),
+                          np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def sphere(nx, ny, nz, xc, yc, zc, R, eta=ETA_W4, py=True):
+    """Sphere fraction 1/2 + 1/2 tanh((R - r) / (sqrt 2 eta)), min-image
+    distances in x and z (and y when periodic)."""
+    x, y, z = _grid3(nx, ny, nz)
+    dx = x - xc
+    dx -= nx * np.round(dx / nx)
+    dz = z - zc
+    dz -= nz * np.round(dz / nz)
+    dy = y - yc
+    if py:
+        dy -= ny * np.round(dy / ny)
+    return _step(R - np.sqrt(dx * dx + dy * dy + dz * dz), eta)
+
+
+def base_params3(N, nx, ny, nz, sigma, **kw) -> dict:
+    """Parameter dict of a D3Q15 grid (keys of base_params plus nz and
+    lattice = 1); gravity has three components."""
+    g = kw.pop("gravity", (0.0, 0.0, 0.0))
+    p = base_params(N, nx, ny, sigma, **kw)
+    p.update(nz=int(nz), lattice=1, gravity=[float(v) for v in g])
+    return p
+
+
+def random_smooth3(seed, N, nx, ny, nz, rho=None, sigma=None, wall_y=0,
+                   precision="fp64", amp_u=0.0, nblobs=4,
+                   gravity=(0.0, 0.0, 0.0)) -> Workload:
+    """Seeded random smooth 3-D mixture (spheres of every phase normalised
+    to sum 1) with an optional smooth velocity, for parity tests."""
+    rng = np.random.default_rng(seed)
+    if sigma is None:
+        sigma = sample_sigma(rng, N)
+    c = np.full((N, nz, ny, nx), 1e-3)
+    for j in range(N):
+        for _ in range(nblobs):
+            xc, yc, zc = rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(0, nz)
+            R = rng.uniform(1.5, max(2.0, min(nx, ny, nz) / 3.0))
+            c[j] += rng.uniform(0.5, 1.0) * sphere(nx, ny, nz, xc, yc, zc, R,
+                                                   py=not wall_y)
+    c /= c.sum(0, keepdims=True)
+    u = None
+    if amp_u:
+        x, y, z = _grid3(nx, ny, nz)
+        ph = rng.uniform(0, 2 * math.pi, size=3)
+        u = np.stack([
+            amp_u * np.sin(2 * math.pi * y / ny + ph[0]) * np.cos(2 * math.pi * z / nz),
+            amp_u * np.sin(2 * math.pi * z / nz + ph[1]) * np.cos(2 * math.pi * x / nx),
+            amp_u * np.sin(2 * math.pi * x / nx + ph[2]) * np.cos(2 * math.pi * y / ny),
+        ])
+    taus = rng.uniform(0.6, 1.2, size=N)
+    mobs = rng.uniform(0.02, 0.2, size=N - 1)
+    p = base_params3(N, nx, ny, nz, sigma, rho=rho, tau=list(taus[1:]),
+                     tau_g=taus[0], mobility=mobs, precision=precision,
+                     wall_y=wall_y, gravity=gravity)
+    return Workload(f"random3_N{N}_{nx}x{ny}x{nz}_s{seed}", p, c, u, 0.0, 0, seed)
+
+
+def sphere_drops3(n=96, N=3, R=16.0, sigma=1e-3, precision="fp32", tau=0.8,
+                  mobility=0.1, steps=2000) -> Workload:
+    """N-1 sphere drops (phases 2..N) in phase 1 on an n^3 periodic D3Q15
+    grid, spaced along x (the 3-D analogue of the static-drop case)."""
+    c = np.zeros((N, n, n, n))
+    for j in range(1, N):
+        c[j] = sphere(n, n, n, n * j / N, n / 2.0, n / 2.0, R)
+    c[0] = 1.0 - c[1:].sum(0)
+    p = base_params3(N, n, n, n, sigma, tau=tau, mobility=mobility,
+                     precision=precision)
+    return Workload(f"sphere_drops3_N{N}_{n}", p, c, None, 0.0, steps)

@@ -1,0 +1,134 @@
+"""Pins of the D3Q15 oracle (the 3-D lattice of Section 3.1) against the
+moment conditions of the appendix, stencil exactness, conservation and
+stationarity (same statements as the 2-D pins, on 15 velocities)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_12553_gb300 import workloads as W
+
+# D3Q15 velocities as printed in Section 3.1 (columns k = 0..14).
+CV = np.array([[0, 1, 0, 0, -1, 0, 0, 1, 1, 1, -1, -1, -1, -1, 1],
+               [0, 0, 1, 0, 0, -1, 0, 1, 1, -1, 1, -1, -1, 1, -1],
+               [0, 0, 0, 1, 0, 0, -1, 1, -1, 1, 1, -1, 1, -1, -1]],
+              dtype=float).T
+CS2 = 1.0 / 3.0
+
+
+def test_geq3_moments():
+    rng = np.random.default_rng(0)
+    d = np.eye(3)
+    for _ in range(30):
+        r0, pr, rho = rng.uniform(-2, 2), rng.uniform(-1e-2, 1e-2), rng.uniform(0.5, 9)
+        u = rng.uniform(-0.1, 0.1, 3)
+        g = oracle.geq3(r0, pr, rho, u)
+        assert abs(g.sum() - r0) < 1e-13
+        np.testing.assert_allclose(CV.T @ g, rho * u, atol=1e-14 * rho)
+        np.testing.assert_allclose(np.einsum("k,ka,kb->ab", g, CV, CV),
+                                   pr * d + rho * np.outer(u, u), atol=1e-14 * rho)
+        want = rho * CS2 * (np.einsum("ab,c->abc", d, u) + np.einsum("ac,b->abc", d, u)
+                            + np.einsum("bc,a->abc", d, u))
+        np.testing.assert_allclose(np.einsum("k,ka,kb,kc->abc", g, CV, CV, CV),
+                                   want, atol=1e-14 * rho)
+
+
+def test_force_dist3_moments():
+    rng = np.random.default_rng(1)
+    for _ in range(30):
+        tg = rng.uniform(0.55, 2.0)
+        u, F, gr, J = (rng.uniform(-1, 1, 3) * s for s in (0.1, 1e-4, 1.0, 1e-3))
+        G = oracle.force_dist3(tg, u, F, gr, J)
+        assert abs(G.sum() - u @ gr) < 1e-15
+        np.testing.assert_allclose(CV.T @ G, F, atol=1e-17)
+        Ju = np.outer(J, u) / (tg - 0.5)
+        want = (np.outer(u, F) + np.outer(F, u) + CS2 * np.outer(u, gr)
+                + CS2 * np.outer(gr, u) + CS2 * (u @ gr) * np.eye(3) + 0.5 * (Ju + Ju.T))
+        np.testing.assert_allclose(np.einsum("k,ka,kb->ab", G, CV, CV), want,
+                                   atol=1e-15)
+
+
+def test_ch3_moments():
+    rng = np.random.default_rng(2)
+    for _ in range(30):
+        a, phi, Ci = rng.uniform(0.1, 3), rng.uniform(-1, 1), rng.uniform(-1e-3, 1e-3)
+        u, up = rng.uniform(-0.1, 0.1, 3), rng.uniform(-0.1, 0.1, 3)
+        pp, tau = rng.uniform(-1, 1), rng.uniform(0.55, 2)
+        h = oracle.heq3(a, phi, Ci, u)
+        assert abs(h.sum() - phi) < 1e-15
+        np.testing.assert_allclose(CV.T @ h, phi * u, atol=1e-16)
+        np.testing.assert_allclose(np.einsum("k,ka,kb->ab", h, CV, CV),
+                                   CS2 * a * Ci * np.eye(3), atol=1e-17)
+        R = oracle.source3(tau, phi, u, pp, up)
+        assert abs(R.sum()) < 1e-17
+        np.testing.assert_allclose(CV.T @ R, (1 - 0.5 / tau) * (phi * u - pp * up),
+                                   atol=1e-16)
+
+
+def test_stencils3_exact_on_quadratics():
+    rng = np.random.default_rng(3)
+    nx, ny, nz = 16, 14, 12
+    p = W.base_params3(3, nx, ny, nz, 1e-3)
+    s = oracle.OracleSim3D(p)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    x, y, z = x.astype(float), y.astype(float), z.astype(float)
+    A = rng.uniform(-1, 1, (3, 3))
+    A = A + A.T
+    b = rng.uniform(-1, 1, 3)
+    X = np.stack([x, y, z])
+    f = 0.5 * np.einsum("aijk,ab,bijk->ijk", X, A, X) + np.einsum("a,aijk->ijk", b, X)
+    grad, lap = s.stencils(f)
+    sl = (slice(2, nz - 2), slice(2, ny - 2), slice(2, nx - 2))
+    want = np.einsum("ab,bijk->aijk", A, X) + b[:, None, None, None]
+    for a in range(3):
+        np.testing.assert_allclose(grad[a][sl], want[a][sl], atol=1e-10)
+    np.testing.assert_allclose(lap[sl], np.trace(A), atol=1e-10)
+    s.close()
+
+
+@pytest.mark.parametrize("wall", [0, 1])
+def test_mass_conservation3(wall):
+    w = W.random_smooth3(5, 4, 10, 9, 8, rho=[3.0, 1.0, 2.0, 5.0], wall_y=wall,
+                         amp_u=0.02, gravity=(0.0, -1e-5, 0.0))
+    s = oracle.OracleSim3D(w.params)
+    s.init(w.c0, w.u0)
+    m0 = s.moments()["phi"].sum((1, 2, 3))
+    s.step(60)
+    m1 = s.moments()["phi"].sum((1, 2, 3))
+    np.testing.assert_allclose(m1, m0, rtol=0, atol=1e-13 * w.c0[0].size)
+    s.close()
+
+
+def test_quiescent3_stationary():
+    N, sh = 3, (6, 7, 5)
+    c = np.broadcast_to(np.array([0.2, 0.3, 0.5])[:, None, None, None], (N,) + sh).copy()
+    p = W.base_params3(N, sh[2], sh[1], sh[0], 1e-3, rho=[2.0, 1.0, 4.0])
+    s = oracle.OracleSim3D(p)
+    s.init(c)
+    s.step(200)
+    m = s.moments()
+    assert np.abs(m["u"]).max() <= 1e-18
+    assert np.ptp(m["phi"], axis=(1, 2, 3)).max() <= 1e-15
+    s.close()
+
+
+def test_2d_fields_reduce_to_d2q9():
+    """A field that does not vary along z does not feel the third
+    dimension through the stencils: Eq. N31 on D3Q15 then equals Eq. N31 on
+    D2Q9 (both are exact on quadratics and second order; for a smooth
+    z-invariant field they agree to the O(h^2) truncation error)."""
+    nx, ny = 24, 20
+    x = np.arange(nx, dtype=float)
+    y = np.arange(ny, dtype=float)[:, None]
+    f2 = np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny)
+    f3 = np.broadcast_to(f2, (4, ny, nx)).copy()
+    s2 = oracle.OracleSim(W.base_params(3, nx, ny, 1e-3))
+    s3 = oracle.OracleSim3D(W.base_params3(3, nx, ny, 4, 1e-3))
+    g2, l2 = s2.stencils(f2)
+    g3, l3 = s3.stencils(f3)
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / ny
+    assert np.abs(g3[2]).max() < 1e-14
+    for a in range(2):
+        assert np.abs(g3[a][0] - g2[a]).max() < 0.5 * (kx ** 2 + ky ** 2)
+    assert np.abs(l3[0] - l2).max() < 0.5 * (kx ** 2 + ky ** 2)
+    s2.close()
+    s3.close()
