@@ -233,6 +233,36 @@ def e2e_run(w, prec, steps):
     return V * steps / t / 1e6, h2d / steps, d2h / steps
 
 
+def d3q15_run(n=256, steps=100):
+    """D3Q15 (three dimensions): three phases, two sphere drops R = n/6 in a
+    periodic n^3 box, FP32 storage, generic 3-D kernel."""
+    import torch
+    from paper_1904_12553_gb300 import Solver, workloads as W
+
+    w = W.sphere_drops3(n=n, N=3, R=n / 6.0, precision="fp32")
+    s = Solver(w.params)
+    s.init(w.c0)
+    s.step(3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(steps):
+        s.step(1)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    N, V = 3, w.V
+    B = 2 * 4 * (15 * (N - 1) + 14 + (N - 1) + 3)
+    peak, _ = peaks()
+    return {"workload": f"N=3 two spheres, D3Q15 {n}^3 periodic, FP32",
+            "mlups": V / (ms / 1e3) / 1e6, "ms_per_step": ms,
+            "alg_bytes_per_node": B,
+            "hbm_frac": B * V / (ms / 1e3) / 1e9 / peak,
+            "kernel": "generic 3-D tile"}
+
+
 def batch_run(steps=50, ncases=256):
     """Batched ensemble (256 seeded static-drop / lens cases, sides 64..512,
     N = 3..5, FP32): one persistent launch per step under a CUDA graph with
@@ -367,6 +397,7 @@ def run_ours(args, dist, rank, world):
                 "hbm_frac": fB * V / (fstep / 1e3) / 1e9 / peak}
     if not args.quick:
         forms["batch"] = batch_run()
+        forms["d3q15_fp32"] = d3q15_run()
     e2e_v, h2d, d2h = e2e_run(w, "fp32", args.steps)
     cpu = cpu_baseline() if (world == 1 and not args.quick) else None
     line = {

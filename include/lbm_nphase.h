@@ -14,8 +14,9 @@
  * populations. Lattice units: dx = dt = 1, c_s^2 = 1/3.
  *
  * Conventions for every function below:
- *  - Arrays are row-major [field][y][x] with x fastest, FP64, node (x, y) at
- *    integer coordinates. Field order: phases 1..N (the paper's indices).
+ *  - Arrays are row-major [field][y][x] (D2Q9) or [field][z][y][x] (D3Q15)
+ *    with x fastest, FP64, nodes at integer coordinates. Field order: phases
+ *    1..N (the paper's indices); velocity fields have D = 2 or 3 components.
  *  - Device work is ordered on the CUDA stream given to lbm_nphase_create
  *    (NULL = the legacy default stream). lbm_nphase_step is asynchronous;
  *    lbm_nphase_init, lbm_nphase_moments and lbm_nphase_diagnostics return
@@ -62,9 +63,12 @@ typedef enum {
 typedef struct {
   int32_t N;           /* number of phases, 2..5 */
   int32_t nx, ny;      /* grid size, >= 1 each */
+  int32_t nz;          /* third dimension of a D3Q15 grid (>= 1); D2Q9: 0 or 1 */
+  int32_t lattice;     /* 0: D2Q9 (two dimensions); 1: D3Q15 (three; Section
+                          3.1), central scheme only */
   int32_t wall_y;      /* 0: periodic in y; 1: halfway bounce-back walls at
-                          y = -1/2 and y = ny - 1/2 (Section 4.2). x is
-                          always periodic. */
+                          y = -1/2 and y = ny - 1/2 (Section 4.2). x (and z)
+                          are always periodic. */
   int32_t precision;   /* lbm_precision */
   int32_t grad_scheme; /* first derivatives: 0 isotropic central scheme,
                           Eq. N31a; 1 isotropic mixed scheme, Eq. N40, read
@@ -78,7 +82,7 @@ typedef struct {
   double tau_g;        /* NS relaxation time > 1/2; nu = (tau_g - 1/2)/3, Eq. N21_1 */
   double tau[LBM_MAX_N - 1];      /* CH relaxation times tau_i > 1/2 */
   double mobility[LBM_MAX_N - 1]; /* m_i > 0; a_i = m_i / (c_s^2 (tau_i - 1/2)), Eq. N30 */
-  double gravity[2];   /* body force G = rho * gravity */
+  double gravity[3];   /* body force G = rho * gravity (x, y, z) */
   double rho0;         /* constant of g_0^eq (Eq. 25); it affects no output */
 } lbm_nphase_params;
 
@@ -115,8 +119,9 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *params,
                              void *d_workspace, size_t workspace_bytes,
                              void *cuda_stream, lbm_nphase_t **out);
 
-/* Initial state from volume fractions c[N][ny][nx] (Eq. N2, sum_k c_k = 1)
- * and velocity u[2][ny][nx] (NULL: fluid at rest), uniform pressure p0.
+/* Initial state from volume fractions c[N][(nz)][ny][nx] (Eq. N2,
+ * sum_k c_k = 1) and velocity u[D][(nz)][ny][nx] (NULL: fluid at rest),
+ * uniform pressure p0.
  * Pointers may be host or device memory. The order parameters follow from
  * the inverse of Eqs. N2 and N12; the distributions start at equilibrium,
  * h = h^eq(phi, C, u) (Eq. N25) and g = g^eq(p0, u) (Eq. 25), and the
@@ -133,8 +138,8 @@ lbm_status lbm_nphase_init(lbm_nphase_t *h, const double *c, const double *u,
  * Errors: LBM_ESTATE before init or after LBM_EUNSTABLE, LBM_ECUDA. */
 lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps);
 
-/* Macroscopic fields at the current time: phi[N-1][ny][nx], c[N][ny][nx],
- * u[2][ny][nx], p[ny][nx], rho[ny][nx] (Eqs. N28, N18, N22_1, N23, N29).
+/* Macroscopic fields at the current time: phi[N-1], c[N], u[D], p, rho,
+ * each field [(nz)][ny][nx] (Eqs. N28, N18, N22_1, N23, N29).
  * Any pointer may be NULL; non-NULL pointers may be host or device memory.
  * Synchronises. */
 lbm_status lbm_nphase_moments(lbm_nphase_t *h, double *phi, double *c,

@@ -33,6 +33,7 @@ class LbmError(RuntimeError):
 class LbmParams(C.Structure):
     _fields_ = [
         ("N", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+        ("nz", C.c_int32), ("lattice", C.c_int32),
         ("wall_y", C.c_int32), ("precision", C.c_int32),
         ("grad_scheme", C.c_int32),
         ("rho", C.c_double * MAXN),
@@ -40,7 +41,7 @@ class LbmParams(C.Structure):
         ("eta", C.c_double), ("beta", C.c_double), ("tau_g", C.c_double),
         ("tau", C.c_double * (MAXN - 1)),
         ("mobility", C.c_double * (MAXN - 1)),
-        ("gravity", C.c_double * 2), ("rho0", C.c_double),
+        ("gravity", C.c_double * 3), ("rho0", C.c_double),
     ]
 
 
@@ -139,6 +140,8 @@ def make_params(p: dict) -> LbmParams:
     N = int(p["N"])
     s = LbmParams()
     s.N, s.nx, s.ny = N, int(p["nx"]), int(p["ny"])
+    s.lattice = int(p.get("lattice", 0))
+    s.nz = int(p.get("nz", 1 if s.lattice == 1 else 0))
     s.wall_y = int(p.get("wall_y", 0))
     prec = p.get("precision", "fp64")
     s.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -154,8 +157,8 @@ def make_params(p: dict) -> LbmParams:
     for i in range(max(0, n - 1)):
         s.tau[i] = float(p["tau"][i])
         s.mobility[i] = float(p["mobility"][i])
-    g = p.get("gravity", (0.0, 0.0))
-    s.gravity[0], s.gravity[1] = float(g[0]), float(g[1])
+    g = list(p.get("gravity", (0.0, 0.0))) + [0.0, 0.0]
+    s.gravity[0], s.gravity[1], s.gravity[2] = float(g[0]), float(g[1]), float(g[2])
     s.rho0 = float(p.get("rho0", 1.0))
     return s
 
@@ -285,7 +288,11 @@ class Solver:
         self.params = dict(params)
         self.N = int(params["N"])
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
-        self.V = self.nx * self.ny
+        self.three_d = int(params.get("lattice", 0)) == 1
+        self.nz = int(params.get("nz", 1)) if self.three_d else 1
+        self.D = 3 if self.three_d else 2
+        self.grid = ((self.nz,) if self.three_d else ()) + (self.ny, self.nx)
+        self.V = self.nx * self.ny * self.nz
         self.device = torch.device(device or "cuda")
         self.stream = stream or torch.cuda.current_stream(self.device)
         nbytes = lbm_nphase_workspace_bytes(params)
@@ -316,9 +323,10 @@ class Solver:
         return a
 
     def init(self, c0, u0=None, p0: float = 0.0):
-        """c0[N][ny][nx], u0[2][ny][nx] (numpy or torch, host or device)."""
-        c = self._dev(c0, (self.N, self.ny, self.nx))
-        u = None if u0 is None else self._dev(u0, (2, self.ny, self.nx))
+        """c0[N][(nz)][ny][nx], u0[D][(nz)][ny][nx] (numpy or torch, host or
+        device)."""
+        c = self._dev(c0, (self.N,) + self.grid)
+        u = None if u0 is None else self._dev(u0, (self.D,) + self.grid)
         lbm_nphase_init(self.handle, c.data_ptr(),
                         None if u is None else u.data_ptr(), p0)
 
@@ -327,10 +335,10 @@ class Solver:
 
     def moments(self, numpy: bool = True) -> dict:
         t = self.torch
-        sh = (self.ny, self.nx)
+        sh = self.grid
         out = {"phi": t.empty((self.N - 1,) + sh, dtype=t.float64, device=self.device),
                "c": t.empty((self.N,) + sh, dtype=t.float64, device=self.device),
-               "u": t.empty((2,) + sh, dtype=t.float64, device=self.device),
+               "u": t.empty((self.D,) + sh, dtype=t.float64, device=self.device),
                "p": t.empty(sh, dtype=t.float64, device=self.device),
                "rho": t.empty(sh, dtype=t.float64, device=self.device)}
         lbm_nphase_moments(self.handle, out["phi"].data_ptr(),

@@ -334,7 +334,7 @@ size_t lbm_nphase_batch_workspace_bytes(const lbm_nphase_params *params,
     if (p.precision != LBM_FP32) return 0;
     lbm_nphase_model m;
     if (lbm_nphase_derive(&p, &m) != LBM_OK || !m.uniform_density ||
-        p.grad_scheme != 0)
+        p.grad_scheme != 0 || p.lattice != 0)
       return 0;
     total += case_bytes(p);
     items += tiles_for(p, 4);

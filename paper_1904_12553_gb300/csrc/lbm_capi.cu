@@ -127,7 +127,13 @@ lbm_status validate(const lbm_nphase_params *p) {
   if (p->N < 2 || p->N > LBM_MAX_N) return LBM_EINVAL;
   if (p->nx < 1 || p->ny < 1 || p->nx > (1 << 20) || p->ny > (1 << 20))
     return LBM_EINVAL;
-  if ((double)p->nx * (double)p->ny > 17179869184.0) return LBM_EINVAL;
+  if (p->lattice != 0 && p->lattice != 1) return LBM_EINVAL;
+  if (p->lattice == 0 && p->nz != 0 && p->nz != 1) return LBM_EINVAL;
+  if (p->lattice == 1 && (p->nz < 1 || p->nz > (1 << 20) || p->grad_scheme != 0))
+    return LBM_EINVAL;
+  if ((double)p->nx * (double)p->ny * (double)(p->nz > 1 ? p->nz : 1) >
+      17179869184.0)
+    return LBM_EINVAL;
   if (p->wall_y != 0 && p->wall_y != 1) return LBM_EINVAL;
   if (p->precision < LBM_FP64 || p->precision > LBM_MIX_FP16) return LBM_EINVAL;
   if (p->grad_scheme != 0 && p->grad_scheme != 1) return LBM_EINVAL;
@@ -147,8 +153,9 @@ lbm_status validate(const lbm_nphase_params *p) {
     if (!finite_pos(p->mobility[i])) return LBM_EINVAL;
   }
   if (!isfinite(p->gravity[0]) || !isfinite(p->gravity[1]) ||
-      !isfinite(p->rho0))
+      !isfinite(p->gravity[2]) || !isfinite(p->rho0))
     return LBM_EINVAL;
+  if (p->lattice == 0 && p->gravity[2] != 0.0) return LBM_EINVAL;
   return LBM_OK;
 }
 
@@ -158,20 +165,25 @@ struct Layout {
   size_t h0, hm, gm, phi_prev, u_prev, stage, red, red_out, err, total;
 };
 
+// Lattice shape: moving directions Q - 1 and velocity components D.
+int moving_dirs(const lbm_nphase_params *p) { return p->lattice == 1 ? 14 : 8; }
+int dims(const lbm_nphase_params *p) { return p->lattice == 1 ? 3 : 2; }
+int depth(const lbm_nphase_params *p) { return p->lattice == 1 ? p->nz : 1; }
+
 Layout layout(const lbm_nphase_params *p) {
-  const size_t V = (size_t)p->nx * p->ny;
-  const int NP = p->N - 1;
+  const size_t V = (size_t)p->nx * p->ny * depth(p);
+  const int NP = p->N - 1, QM = moving_dirs(p), D = dims(p);
   const size_t sT = p->precision == LBM_FP64 ? 8 : 4;
   const size_t sS = p->precision == LBM_FP64 ? 8 : (p->precision == LBM_FP32 ? 4 : 2);
-  const size_t tiles = (size_t)lbm::tiles_x(p->nx) * lbm::tiles_y(p->ny);
+  const size_t tiles = lbm::tiles_total(p->lattice, p->nx, p->ny, depth(p));
   Layout L;
   size_t off = 0;
   L.h0 = off;       off += 2 * align256(NP * V * sT);
-  L.hm = off;       off += 2 * align256(NP * 8 * V * sS);
-  L.gm = off;       off += 2 * align256(8 * V * sS);
+  L.hm = off;       off += 2 * align256(NP * QM * V * sS);
+  L.gm = off;       off += 2 * align256(QM * V * sS);
   L.phi_prev = off; off += 2 * align256(NP * V * sT);
-  L.u_prev = off;   off += align256(2 * V * sT);
-  L.stage = off;    off += align256((p->N + 2) * V * 8);
+  L.u_prev = off;   off += align256(D * V * sT);
+  L.stage = off;    off += align256((p->N + D) * V * 8);
   L.red = off;      off += align256(tiles * (p->N + 2) * 8);
   L.red_out = off;  off += align256(8 * 8);
   L.err = off;      off += align256(sizeof(int));
@@ -268,6 +280,15 @@ namespace lbm {
 cudaError_t launch_tile(int prec, const Consts &k, const Grid &g, int cur,
                         int mode, const Outputs &o, bool nonunif, bool wall,
                         cudaStream_t s) {
+  if (g.lattice == 1) {
+    switch (prec) {
+      case LBM_FP64: return launch_tile3_f64(k, g, cur, mode, o, nonunif, wall, s);
+      case LBM_FP32: return launch_tile3_f32(k, g, cur, mode, o, nonunif, wall, s);
+      case LBM_MIX_BF16: return launch_tile3_bf16(k, g, cur, mode, o, nonunif, wall, s);
+      case LBM_MIX_FP16: return launch_tile3_f16(k, g, cur, mode, o, nonunif, wall, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (prec) {
     case LBM_FP64: return launch_tile_f64(k, g, cur, mode, o, nonunif, wall, s);
     case LBM_FP32: return launch_tile_f32(k, g, cur, mode, o, nonunif, wall, s);
@@ -280,6 +301,15 @@ cudaError_t launch_tile(int prec, const Consts &k, const Grid &g, int cur,
 cudaError_t launch_init(int prec, const Consts &k, const Grid &g, int cur,
                         const double *c, const double *u, double p0, bool wall,
                         cudaStream_t s) {
+  if (g.lattice == 1) {
+    switch (prec) {
+      case LBM_FP64: return launch_init3_f64(k, g, cur, c, u, p0, wall, s);
+      case LBM_FP32: return launch_init3_f32(k, g, cur, c, u, p0, wall, s);
+      case LBM_MIX_BF16: return launch_init3_bf16(k, g, cur, c, u, p0, wall, s);
+      case LBM_MIX_FP16: return launch_init3_f16(k, g, cur, c, u, p0, wall, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (prec) {
     case LBM_FP64: return launch_init_f64(k, g, cur, c, u, p0, wall, s);
     case LBM_FP32: return launch_init_f32(k, g, cur, c, u, p0, wall, s);
@@ -424,6 +454,7 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   k.jfac = 1.0 / (p->tau_g - 0.5);
   k.grav[0] = p->gravity[0];
   k.grav[1] = p->gravity[1];
+  k.grav[2] = p->gravity[2];
   k.rho_base = N / Gam;
   // 16-bit storage: h_k / w_k and g_k / w_k are O(1e-4 .. 1e-1) for the
   // model's parameter ranges; 2^12 keeps them in FP16's normal range.
@@ -432,12 +463,15 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   Grid &g = h->g;
   g.nx = p->nx;
   g.ny = p->ny;
-  g.V = (size_t)p->nx * p->ny;
+  g.nz = depth(p);
+  g.lattice = p->lattice;
+  g.V = (size_t)p->nx * p->ny * g.nz;
   char *base = (char *)ws;
   const size_t sT = h->prec == LBM_FP64 ? 8 : 4;
   const size_t sS = h->prec == LBM_FP64 ? 8 : (h->prec == LBM_FP32 ? 4 : 2);
-  const size_t h0b = align256(n * g.V * sT), hmb = align256(n * 8 * g.V * sS),
-               gmb = align256(8 * g.V * sS);
+  const int QM = moving_dirs(p);
+  const size_t h0b = align256(n * g.V * sT), hmb = align256(n * QM * g.V * sS),
+               gmb = align256(QM * g.V * sS);
   for (int b = 0; b < 2; ++b) {
     g.h0[b] = base + L.h0 + b * h0b;
     g.hm[b] = base + L.hm + b * hmb;
@@ -453,7 +487,7 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   g.err = (int *)(base + L.err);
   g.grad_scheme = p->grad_scheme;
   g.use_tma = false;
-  if (tma_allowed() && !h->nonunif && p->grad_scheme == 0) {
+  if (tma_allowed() && !h->nonunif && p->grad_scheme == 0 && p->lattice == 0) {
     lbm::EncodeTiledFn enc = tensor_map_encoder();
     switch (h->prec) {
       case LBM_FP32: g.use_tma = lbm::encode_tma_f32(k, g, enc); break;
@@ -487,7 +521,7 @@ lbm_status lbm::init_at(lbm_nphase_t *h, const double *c, const double *u,
     dc = h->stage;
   }
   if (u && !is_device_ptr(u)) {
-    e = cudaMemcpyAsync(h->stage + N * V, u, 2 * V * sizeof(double),
+    e = cudaMemcpyAsync(h->stage + N * V, u, dims(&h->prm) * V * sizeof(double),
                         cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
     du = h->stage + N * V;
@@ -571,7 +605,8 @@ struct StateHeader {
   int32_t N, nx, ny, precision, wall_y, grad_scheme;
   int64_t steps;
   uint64_t payload;  // bytes after the header
-  uint8_t pad[16];
+  int32_t nz, lattice;
+  uint8_t pad[8];
 };
 static_assert(sizeof(StateHeader) == 64, "state header");
 
@@ -586,11 +621,12 @@ int state_parts(const lbm_nphase_t *h, Part out[5]) {
   const size_t sT = h->prec == LBM_FP64 ? 8 : 4;
   const size_t sS = h->prec == LBM_FP64 ? 8 : (h->prec == LBM_FP32 ? 4 : 2);
   const int c = h->cur;
+  const int QM = moving_dirs(&h->prm), D = dims(&h->prm);
   out[0] = {h->g.h0[c], n * V * sT};
-  out[1] = {h->g.hm[c], n * 8 * V * sS};
-  out[2] = {h->g.gm[c], 8 * V * sS};
+  out[1] = {h->g.hm[c], n * QM * V * sS};
+  out[2] = {h->g.gm[c], QM * V * sS};
   out[3] = {h->g.phi_prev[c], n * V * sT};
-  out[4] = {h->g.u_prev, 2 * V * sT};
+  out[4] = {h->g.u_prev, D * V * sT};
   return 5;
 }
 }  // namespace
@@ -616,6 +652,8 @@ lbm_status lbm_nphase_get_state(lbm_nphase_t *h, void *dst, size_t bytes) {
   hd.precision = h->prm.precision;
   hd.wall_y = h->prm.wall_y;
   hd.grad_scheme = h->prm.grad_scheme;
+  hd.nz = depth(&h->prm);
+  hd.lattice = h->prm.lattice;
   hd.steps = h->steps;
   hd.payload = lbm_nphase_state_bytes(h) - sizeof(hd);
   const bool dev = is_device_ptr(dst);
@@ -644,7 +682,8 @@ lbm_status lbm_nphase_set_state(lbm_nphase_t *h, const void *src, size_t bytes) 
                              dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
   if (e != cudaSuccess) return cuda_fail(h, e);
   if (memcmp(hd.magic, "LBMNPHS1", 8) != 0 || hd.N != h->prm.N ||
-      hd.nx != h->prm.nx || hd.ny != h->prm.ny ||
+      hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.nz != depth(&h->prm) ||
+      hd.lattice != h->prm.lattice ||
       hd.precision != h->prm.precision ||
       hd.payload != lbm_nphase_state_bytes(h) - sizeof(hd))
     return LBM_EINVAL;
@@ -673,7 +712,7 @@ lbm_status lbm_nphase_moments(lbm_nphase_t *h, double *phi, double *c,
   const size_t V = h->g.V;
   const int N = h->prm.N;
   double *ptr[5] = {phi, c, u, p, rho};
-  const int nf[5] = {N - 1, N, 2, 1, 1};
+  const int nf[5] = {N - 1, N, dims(&h->prm), 1, 1};
   Outputs dev = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double **dslot[5] = {&dev.phi, &dev.c, &dev.u, &dev.p, &dev.rho};
   bool any_dev = false, any_host = false;
@@ -722,7 +761,7 @@ lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
   cudaError_t e = lbm::launch_tile(h->prec, h->k, h->g, h->cur, lbm::MODE_DIAG,
                                    none, h->nonunif, h->wall, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  const int nparts = lbm::tiles_x(h->g.nx) * lbm::tiles_y(h->g.ny);
+  const int nparts = (int)lbm::tiles_total(h->g.lattice, h->g.nx, h->g.ny, h->g.nz);
   e = lbm::launch_reduce(h->g, nparts, N + 2, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   double r[LBM_MAX_N + 2];
@@ -795,8 +834,10 @@ extern "C" lbm_status lbm_nphase_diagnostics_static(lbm_nphase_t *h,
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(h, e);
   if (dev != h->device || dev < 0 || dev >= kMaxDevices) return LBM_EINVAL;
-  const int nparts = lbm::tiles_x(h->g.nx) * lbm::tiles_y(h->g.ny);
-  if (nparts > LBM_STATIC_MAX_PARTIALS) return LBM_EINVAL;
+  const size_t nparts_z =
+      lbm::tiles_total(h->g.lattice, h->g.nx, h->g.ny, h->g.nz);
+  if (nparts_z > LBM_STATIC_MAX_PARTIALS) return LBM_EINVAL;
+  const int nparts = (int)nparts_z;
   double *base;
   {
     // First call on a device: look up the array's device address with that

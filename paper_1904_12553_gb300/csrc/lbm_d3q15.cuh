@@ -1,0 +1,530 @@
+// Three-dimensional variant on the D3Q15 lattice (Section 3.1): the same
+// time step as the D2Q9 kernels with 15 velocities and the 14-neighbour
+// stencils of Eq. N31. Grids are nx x ny x nz, node (x, y, z) at
+// (z ny + y) nx + x, periodic in x and z, periodic or walled in y.
+//
+// Layout (per phase i): rest slot [i][V], moving populations [i][k-1][V]
+// for k = 1..14, NS populations [k-1][V], phi(t-1) [i][V], u(t-1) [3][V].
+// Included by lbm_kernels.cuh; instantiated per storage precision.
+#pragma once
+
+namespace lbm {
+
+// D3Q15 (Section 3.1): 0 rest; 1..6 the faces (+x, +y, +z, -x, -y, -z);
+// 7..14 the corners.
+__host__ __device__ constexpr int c3x(int k) {
+  return (k == 1 || k == 7 || k == 8 || k == 9 || k == 14) ? 1
+         : (k == 4 || k == 10 || k == 11 || k == 12 || k == 13) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3y(int k) {
+  return (k == 2 || k == 7 || k == 8 || k == 10 || k == 13) ? 1
+         : (k == 5 || k == 9 || k == 11 || k == 12 || k == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3z(int k) {
+  return (k == 3 || k == 7 || k == 9 || k == 10 || k == 12) ? 1
+         : (k == 6 || k == 8 || k == 11 || k == 13 || k == 14) ? -1 : 0;
+}
+template <typename T>
+__host__ __device__ constexpr T w3_of(int k) {
+  return k == 0 ? T(2) / T(9) : (k <= 6 ? T(1) / T(9) : T(1) / T(72));
+}
+__host__ __device__ constexpr int opp3(int k) {
+  return k == 0 ? 0 : (k <= 6 ? (k <= 3 ? k + 3 : k - 3)
+                              : (k == 7 ? 11 : k == 11 ? 7 : k == 8 ? 12 : k == 12 ? 8
+                                 : k == 9 ? 13 : k == 13 ? 9 : k == 10 ? 14 : 10));
+}
+static_assert(c3x(opp3(8)) == -c3x(8) && c3y(opp3(8)) == -c3y(8) &&
+                  c3z(opp3(8)) == -c3z(8) && c3x(opp3(10)) == -c3x(10) &&
+                  c3y(opp3(13)) == -c3y(13) && c3z(opp3(9)) == -c3z(9),
+              "D3Q15 opposites");
+
+constexpr int BX3 = 32, BY3 = 4, BZ3 = 2, NT3 = BX3 * BY3 * BZ3;
+
+template <int P> struct KArgs3 {
+  KArgs<P> a;  // pointers, constants (u_prev holds 3 planes)
+  int nz;
+};
+
+// Stencils of Eq. N31 on a shared box (strides W, W * H): D3Q15 sums folded
+// over the 7 pairs of opposite velocities.
+template <typename T, int W, int H>
+__device__ __forceinline__ void stencil3(const T *s, int lz, int ly, int lx,
+                                         T *g, T &lap) {
+  const int o = (lz * H + ly) * W + lx;
+  const T c = s[o];
+  T gx = T(0), gy = T(0), gz = T(0), l = T(0);
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    if (opp3(k) < k) continue;  // one of each pair
+    const int d = (c3z(k) * H + c3y(k)) * W + c3x(k);
+    const T p = s[o + d], m = s[o - d];
+    const T wd = w3_of<T>(k) * (p - m);
+    gx += T(c3x(k)) * wd;
+    gy += T(c3y(k)) * wd;
+    gz += T(c3z(k)) * wd;
+    l += w3_of<T>(k) * (p + m - T(2) * c);
+  }
+  // pairs counted once: gradient 2 * sum / (2 c_s^2) = 3 sum; laplacian
+  // 2 * sum / c_s^2 = 6 sum
+  g[0] = T(3) * gx;
+  g[1] = T(3) * gy;
+  g[2] = T(3) * gz;
+  lap = T(6) * l;
+}
+
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T load_hm3(const KArgs<P> &a, int i,
+                                                        int k, size_t q) {
+  return to_T(ldg(a.hm_in + ((size_t)(i * 14 + k - 1)) * a.V + q));
+}
+
+// phi_i at node q from the stored values (FP64: sum of the 15; other forms:
+// phi(t-1) + (d_0 + sum_k h_k), TwoSum error in err).
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T node_phi3(const KArgs<P> &a, int i,
+                                                         size_t q,
+                                                         typename Prec<P>::T &err) {
+  typedef typename Prec<P>::T T;
+  T small = ldg(a.h0_in + (size_t)i * a.V + q);
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    const T x = load_hm3<P>(a, i, k, q);
+    if constexpr (Prec<P>::MIX)
+      small = __fmaf_rn(w3_of<T>(k) * a.sh_ld, x, small);
+    else
+      small = __fadd_rn_T(small, x);
+  }
+  if constexpr (P == LBM_FP64) {
+    err = T(0);
+    return small;
+  } else {
+    const T pp = ldg(a.pp_in + (size_t)i * a.V + q);
+    const T s = __fadd_rn(pp, small);
+    const T bb = __fsub_rn(s, pp);
+    err = __fadd_rn(__fsub_rn(pp, __fsub_rn(s, bb)), __fsub_rn(small, bb));
+    return s;
+  }
+}
+
+template <bool WALL>
+__device__ __forceinline__ size_t node3(int x, int y, int z, int nx, int ny,
+                                        int nz) {
+  return ((size_t)wrap(z, nz) * ny + wrap_y<WALL>(y, ny)) * nx + wrap(x, nx);
+}
+
+template <int P, int NP, bool NU, bool WALL>
+__global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
+  typedef typename Prec<P>::T T;
+  const KArgs<P> &a = A.a;
+  constexpr int RC = NU ? 1 : 0;       // C ring radius
+  constexpr int R = RC + 1;            // phi halo radius
+  constexpr int W = BX3 + 2 * R, H = BY3 + 2 * R, D = BZ3 + 2 * R, PL = W * H * D;
+  constexpr int CW = BX3 + 2 * RC, CH = BY3 + 2 * RC, CD = BZ3 + 2 * RC,
+                CPL = CW * CH * CD;
+  extern __shared__ __align__(16) unsigned char smem3[];
+  T *sphi = (T *)smem3;
+  T *sC = sphi + NP * PL;
+  __shared__ double sred[NT3 / 32][8];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int tid = (tz * BY3 + ty) * BX3 + tx;
+  const int nx = a.nx, ny = a.ny, nz = A.nz;
+  const size_t V = a.V;
+  const int x0 = blockIdx.x * BX3, y0 = blockIdx.y * BY3, z0 = blockIdx.z * BZ3;
+  const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+  const bool active = gx < nx && gy < ny && gz < nz;
+
+  // 1. phi on the box (tile + halo R), wrapped / ghost coordinates.
+  for (int r = tid; r < PL; r += NT3) {
+    const int lx = r % W, ly = (r / W) % H, lz = r / (W * H);
+    const size_t q = node3<WALL>(x0 - R + lx, y0 - R + ly, z0 - R + lz, nx, ny, nz);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T e;
+      sphi[i * PL + r] = node_phi3<P>(a, i, q, e);
+    }
+  }
+  __syncthreads();
+  // 2. Unequal densities: C on the tile and a ring of radius 1; wall ghost
+  //    layers of C repeat the adjacent fluid layer.
+  if constexpr (NU) {
+    for (int r = tid; r < CPL; r += NT3) {
+      const int cx = r % CW, cy = (r / CW) % CH, cz = r / (CW * CH);
+      T ph[NP], lp[NP], cc[NP + 1], rho, hf[NP], gtmp[3];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        ph[i] = sphi[i * PL + ((cz + 1) * H + cy + 1) * W + cx + 1];
+        stencil3<T, W, H>(sphi + i * PL, cz + 1, cy + 1, cx + 1, gtmp, lp[i]);
+      }
+      local_algebra<P, NP>(a, ph, cc, rho, hf);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T Ci = a.bulk * hf[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+        sC[i * CPL + r] = Ci;
+      }
+    }
+    __syncthreads();
+    if constexpr (WALL) {
+      for (int r = tid; r < CPL; r += NT3) {
+        const int cx = r % CW, cy = (r / CW) % CH, cz = r / (CW * CH);
+        const int yg = y0 - 1 + cy;
+        if (yg < 0 || yg >= ny) {
+          const int cys = (yg < 0 ? 0 : ny - 1) - y0 + 1;
+#pragma unroll
+          for (int i = 0; i < NP; ++i)
+            sC[i * CPL + r] = sC[i * CPL + (cz * CH + cys) * CW + cx];
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // 3. Own node: stencils, C, F, u, p.
+  const size_t q = active ? (((size_t)gz * ny + gy) * nx + gx) : 0;
+  const int lz = tz + R, ly = ty + R, lx = tx + R;
+  T ph[NP], gp[NP][3], Cv[NP], cc[NP + 1], rho;
+  {
+    T lp[NP], hf[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      ph[i] = sphi[i * PL + (lz * H + ly) * W + lx];
+      stencil3<T, W, H>(sphi + i * PL, lz, ly, lx, gp[i], lp[i]);
+    }
+    local_algebra<P, NP>(a, ph, cc, rho, hf);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      if constexpr (NU) {
+        Cv[i] = sC[i * CPL + ((tz + 1) * CH + ty + 1) * CW + tx + 1];
+      } else {
+        T Ci = a.bulk * hf[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+        Cv[i] = Ci;
+      }
+    }
+  }
+  T gr[3] = {T(0), T(0), T(0)}, J[3] = {T(0), T(0), T(0)};
+  if constexpr (NU) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T cg[3], dummy;
+      stencil3<T, CW, CH>(sC + i * CPL, tz + 1, ty + 1, tx + 1, cg, dummy);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        J[d] -= a.kmob[i] * cg[d];
+        gr[d] += a.kap[i] * gp[i][d];
+      }
+    }
+  }
+  T F[3];
+  const T grav[3] = {a.grav[0], a.grav[1], A.a.grav_z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d] = rho * grav[d];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) F[d] += Cv[i] * gp[i][d];
+  }
+  T g[15], mo[3] = {T(0), T(0), T(0)}, sg = T(0);
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    g[k] = active ? to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q)) : T(0);
+    T gk = g[k];
+    if constexpr (Prec<P>::MIX) gk *= w3_of<T>(k) * a.sg_ld;
+    mo[0] += T(c3x(k)) * gk;
+    mo[1] += T(c3y(k)) * gk;
+    mo[2] += T(c3z(k)) * gk;
+    sg += gk;
+  }
+  const T rinv = T(1) / rho;
+  T u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = (mo[d] + T(0.5) * F[d]) * rinv;
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
+  // Eq. N23 on D3Q15: c_s^2 / (1 - w_0) = 3/7, s_0 = -w_0 |u|^2 / (2 c_s^2)
+  const T pr = T(3.0 / 7.0) * (sg + T(0.5) * ugr - rho * T(2.0 / 9.0) * T(1.5) * uu);
+
+  if (a.mode == MODE_MOMENTS) {
+    if (!active) return;
+    if (a.o_phi)
+      for (int i = 0; i < NP; ++i) a.o_phi[(size_t)i * V + q] = (double)ph[i];
+    if (a.o_c)
+      for (int k = 0; k <= NP; ++k) a.o_c[(size_t)k * V + q] = (double)cc[k];
+    if (a.o_u)
+      for (int d = 0; d < 3; ++d) a.o_u[(size_t)d * V + q] = (double)u[d];
+    if (a.o_p) a.o_p[q] = (double)pr;
+    if (a.o_rho) a.o_rho[q] = (double)rho;
+    return;
+  }
+  if (a.mode == MODE_DIAG) {
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k <= NP + 2; ++k) {
+      double v;
+      if (k <= NP) v = active ? (double)cc[k] : 0.0;
+      else if (k == NP + 1) v = active ? 0.5 * (double)rho * (double)uu : 0.0;
+      else v = active ? sqrt((double)uu) : 0.0;
+      v = (k == NP + 2) ? warp_max(v) : warp_sum(v);
+      if (lane == 0) sred[wid][k] = v;
+    }
+    __syncthreads();
+    if (tid <= NP + 2) {
+      double v = sred[0][tid];
+      for (int w = 1; w < NT3 / 32; ++w)
+        v = (tid == NP + 2) ? fmax(v, sred[w][tid]) : v + sred[w][tid];
+      const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      a.red[b * (NP + 3) + tid] = v;
+    }
+    return;
+  }
+  if (!active) return;
+
+  // 4. Collisions (Eqs. 24, N24 with Eqs. 25, N20_1, N25-N27), folded as in
+  //    the D2Q9 kernels, and push streaming.
+  size_t dst[15];
+  int dk[15];
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    const int yy = gy + c3y(k);
+    if (WALL && (yy < 0 || yy >= ny)) {
+      dst[k] = q;
+      dk[k] = opp3(k);
+    } else {
+      dst[k] = node3<WALL>(gx + c3x(k), yy, gz + c3z(k), nx, ny, nz);
+      dk[k] = k;
+    }
+  }
+  constexpr bool MIX = Prec<P>::MIX;
+  const T tg = a.tg_inv, ff = a.ffac;
+  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const T Ju = (J[0] * u[0] + J[1] * u[1] + J[2] * u[2]) * a.jfac;
+  const T A0 = tg * (T(3) * pr - T(1.5) * rho * uu) - ff * (T(3) * uF + T(1.5) * Ju);
+  const T B1 = T(3) * tg * rho, B2 = T(4.5) * tg * rho;
+  const T C1 = T(3) * ff, D1 = T(9) * ff, E1 = T(3) * ff, E2 = T(4.5) * ff * a.jfac;
+  const T keep_g = T(1) - tg;
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    const T cx = T(c3x(k)), cy = T(c3y(k)), cz = T(c3z(k));
+    const T cu = cx * u[0] + cy * u[1] + cz * u[2];
+    const T cF = cx * F[0] + cy * F[1] + cz * F[2];
+    T inner = B1 + B2 * cu + D1 * cF;
+    if constexpr (NU)
+      inner += E1 * (cx * gr[0] + cy * gr[1] + cz * gr[2]) +
+               E2 * (cx * J[0] + cy * J[1] + cz * J[2]);
+    const T t = A0 + C1 * cF + cu * inner;
+    if constexpr (MIX)
+      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] =
+          to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
+    else
+      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = keep_g * g[k] + w3_of<T>(k) * t;
+  }
+  const T up[3] = {a.u_prev[q], a.u_prev[V + q], a.u_prev[2 * V + q]};
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const T pp = ldg(a.pp_in + (size_t)i * V + q);
+    const T ti = a.tau_inv[i], aC = a.a[i] * Cv[i];
+    T al = ti * aC, b[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      b[d] = T(3) * (ti * ph[i] * u[d] + a.src[i] * (ph[i] * u[d] - pp * up[d]));
+    if constexpr (MIX) {
+      al *= a.sh_st;
+      for (int d = 0; d < 3; ++d) b[d] *= a.sh_st;
+    }
+    const T keep = T(1) - ti;
+    T moving_sum = T(0), perr;
+    // recompute phi's rounding error of this node (stored values unchanged)
+    node_phi3<P>(a, i, q, perr);
+#pragma unroll
+    for (int k = 1; k < 15; ++k) {
+      const T t = al + T(c3x(k)) * b[0] + T(c3y(k)) * b[1] + T(c3z(k)) * b[2];
+      const T hk = load_hm3<P>(a, i, k, q);
+      const size_t o = ((size_t)(i * 14 + dk[k] - 1)) * V + dst[k];
+      if constexpr (MIX) {
+        const auto sv = to_S<typename Prec<P>::Sm>(keep * hk + t);
+        a.hm_out[o] = sv;
+        moving_sum = __fmaf_rn(w3_of<T>(k) * a.sh_ld, to_T(sv), moving_sum);
+      } else {
+        const T hs = keep * hk + w3_of<T>(k) * t;
+        a.hm_out[o] = hs;
+        moving_sum = __fadd_rn_T(moving_sum, hs);
+      }
+    }
+    T rest;
+    if constexpr (P == LBM_FP64) {
+      const T h0 = ldg(a.h0_in + (size_t)i * V + q);
+      rest = keep * h0 + ti * (ph[i] + (w3_of<T>(0) - T(1)) * aC);
+    } else {
+      rest = __fsub_rn(perr, moving_sum);
+    }
+    a.h0_out[(size_t)i * V + q] = rest;
+    a.pp_out[(size_t)i * V + q] = ph[i];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) a.u_prev[(size_t)d * V + q] = u[d];
+}
+
+template <int P, int NP>
+__global__ void init3_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
+                                 const double *__restrict__ u, double r0,
+                                 double r1, double r2, double r3, double r4) {
+  typedef typename Prec<P>::T T;
+  const double rt[5] = {r0, r1, r2, r3, r4};
+  const double rN = rt[NP];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < a.V;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const double cN = c[(size_t)NP * a.V + q];
+    for (int i = 0; i < NP; ++i) {
+      const double ci = c[(size_t)i * a.V + q];
+      a.pp_out[(size_t)i * a.V + q] =
+          (T)((2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN));
+    }
+    for (int d = 0; d < 3; ++d) a.u_prev[(size_t)d * a.V + q] = u ? (T)u[(size_t)d * a.V + q] : T(0);
+  }
+}
+
+template <int P, int NP, bool WALL>
+__global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
+  typedef typename Prec<P>::T T;
+  typedef typename Prec<P>::Sm Sm;
+  const KArgs<P> &a = A.a;
+  const int nx = a.nx, ny = a.ny, nz = A.nz;
+  const size_t V = a.V;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < V;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(q % nx), y = (int)((q / nx) % ny), z = (int)(q / ((size_t)nx * ny));
+    T ph[NP], lp[NP];
+    for (int i = 0; i < NP; ++i) {
+      const T *f = a.pp_out + (size_t)i * V;
+      T s[27];
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx)
+            s[((dz + 1) * 3 + dy + 1) * 3 + dx + 1] = f[node3<WALL>(x + dx, y + dy, z + dz, nx, ny, nz)];
+      T gtmp[3];
+      ph[i] = s[13];
+      stencil3<T, 3, 3>(s, 1, 1, 1, gtmp, lp[i]);
+    }
+    T cc[NP + 1], rho, hf[NP];
+    local_algebra<P, NP>(a, ph, cc, rho, hf);
+    const T u[3] = {a.u_prev[q], a.u_prev[V + q], a.u_prev[2 * V + q]};
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T p0 = (T)p0d;
+    for (int k = 1; k < 15; ++k) {
+      const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
+      const T geq = w3_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+      if constexpr (Prec<P>::MIX)
+        a.gm_out[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w3_of<T>(k)));
+      else
+        a.gm_out[(size_t)(k - 1) * V + q] = geq;
+    }
+    for (int i = 0; i < NP; ++i) {
+      T Ci = a.bulk * hf[i];
+      for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+      const T aC = a.a[i] * Ci;
+      T moving = T(0);
+      for (int k = 1; k < 15; ++k) {
+        const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
+        const T heq = w3_of<T>(k) * (aC + T(3) * ph[i] * cu);
+        if constexpr (Prec<P>::MIX) {
+          const Sm sv = to_S<Sm>(heq * (a.sh_st / w3_of<T>(k)));
+          a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = sv;
+          moving = __fmaf_rn(w3_of<T>(k) * a.sh_ld, to_T(sv), moving);
+        } else {
+          a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = heq;
+          moving = __fadd_rn_T(moving, heq);
+        }
+      }
+      if constexpr (P == LBM_FP64)
+        a.h0_out[(size_t)i * V + q] = ph[i] + (w3_of<T>(0) - T(1)) * aC;
+      else
+        a.h0_out[(size_t)i * V + q] = -moving;
+    }
+  }
+}
+
+template <int P, int NP, bool NU, bool WALL>
+cudaError_t launch_tile3_t(const Consts &c, const Grid &g, int cur, int mode,
+                           const Outputs &o, cudaStream_t s) {
+  typedef typename Prec<P>::T T;
+  KArgs3<P> A;
+  A.a = make_args<P>(c, g, cur, mode, o);
+  A.nz = g.nz;
+  constexpr int RC = NU ? 1 : 0, R = RC + 1;
+  constexpr size_t smem = (size_t)NP * ((BX3 + 2 * R) * (BY3 + 2 * R) * (BZ3 + 2 * R) +
+                                        (NU ? (BX3 + 2) * (BY3 + 2) * (BZ3 + 2) : 0)) *
+                          sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tile3_kernel<P, NP, NU, WALL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(tiles3_x(g.nx), tiles3_y(g.ny), tiles3_z(g.nz)), block(BX3, BY3, BZ3);
+  tile3_kernel<P, NP, NU, WALL><<<grid, block, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <int P, int NP>
+cudaError_t launch_tile3_np(const Consts &c, const Grid &g, int cur, int mode,
+                            const Outputs &o, bool nonunif, bool wall,
+                            cudaStream_t s) {
+  if (nonunif)
+    return wall ? launch_tile3_t<P, NP, true, true>(c, g, cur, mode, o, s)
+                : launch_tile3_t<P, NP, true, false>(c, g, cur, mode, o, s);
+  return wall ? launch_tile3_t<P, NP, false, true>(c, g, cur, mode, o, s)
+              : launch_tile3_t<P, NP, false, false>(c, g, cur, mode, o, s);
+}
+
+template <int P>
+cudaError_t launch_tile3_p(const Consts &c, const Grid &g, int cur, int mode,
+                           const Outputs &o, bool nonunif, bool wall,
+                           cudaStream_t s) {
+  switch (c.NP) {
+    case 1: return launch_tile3_np<P, 1>(c, g, cur, mode, o, nonunif, wall, s);
+    case 2: return launch_tile3_np<P, 2>(c, g, cur, mode, o, nonunif, wall, s);
+    case 3: return launch_tile3_np<P, 3>(c, g, cur, mode, o, nonunif, wall, s);
+    case 4: return launch_tile3_np<P, 4>(c, g, cur, mode, o, nonunif, wall, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int NP>
+cudaError_t launch_init3_np(const Consts &c, const Grid &g, int cur,
+                            const double *cin, const double *uin, double p0,
+                            bool wall, cudaStream_t s) {
+  KArgs3<P> A;
+  A.a = make_args<P>(c, g, cur ^ 1, MODE_STEP, Outputs{});
+  A.nz = g.nz;
+  const int threads = 256;
+  size_t blocks = (g.V + threads - 1) / threads;
+  if (blocks > 65535u * 16u) blocks = 65535u * 16u;
+  init3_phi_kernel<P, NP><<<(unsigned)blocks, threads, 0, s>>>(
+      A.a, cin, uin, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (wall)
+    init3_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(A, p0);
+  else
+    init3_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(A, p0);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_init3_p(const Consts &c, const Grid &g, int cur,
+                           const double *cin, const double *uin, double p0,
+                           bool wall, cudaStream_t s) {
+  switch (c.NP) {
+    case 1: return launch_init3_np<P, 1>(c, g, cur, cin, uin, p0, wall, s);
+    case 2: return launch_init3_np<P, 2>(c, g, cur, cin, uin, p0, wall, s);
+    case 3: return launch_init3_np<P, 3>(c, g, cur, cin, uin, p0, wall, s);
+    case 4: return launch_init3_np<P, 4>(c, g, cur, cin, uin, p0, wall, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

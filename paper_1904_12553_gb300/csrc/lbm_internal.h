@@ -28,7 +28,7 @@ struct Consts {
   double tg_inv;       // 1 / tau_g
   double ffac;         // 1 - 1/(2 tau_g) (Eq. 24)
   double jfac;         // 1 / (tau_g - 1/2) (Eq. N20_1)
-  double grav[2];      // G = rho * grav
+  double grav[3];      // G = rho * grav
   double off[4], mul[4];  // varphi_j = off_j + mul_j phi_j (Eq. N12)
   double c0[5];        // gamma~_k / Gamma (Eq. N18)
   double Q[5][4];      // gamma~_k delta_kj - gamma~_k gamma~_j / Gamma
@@ -54,7 +54,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType,
 
 // Device state of one grid. Buffers [0] and [1] alternate every step.
 struct Grid {
-  int nx, ny;
+  int nx, ny, nz;   // nz = 1 for D2Q9
+  int lattice;      // 0 D2Q9, 1 D3Q15
   size_t V;
   void *h0[2];      // rest slots: h^i_0 (FP64) or h^i_0 - phi_i(t-1): [N-1][V]
   void *hm[2];      // moving populations h^i_k, k = 1..8: [N-1][8][V]
@@ -89,7 +90,12 @@ cudaError_t launch_reduce(const Grid &g, int nparts, int nvals, cudaStream_t s);
   cudaError_t launch_init_##SUFFIX(const Consts &, const Grid &, int,         \
                                    const double *, const double *, double,    \
                                    bool, cudaStream_t);                       \
-  bool encode_tma_##SUFFIX(const Consts &, Grid &, EncodeTiledFn);
+  bool encode_tma_##SUFFIX(const Consts &, Grid &, EncodeTiledFn);           \
+  cudaError_t launch_tile3_##SUFFIX(const Consts &, const Grid &, int, int,   \
+                                    const Outputs &, bool, bool, cudaStream_t);\
+  cudaError_t launch_init3_##SUFFIX(const Consts &, const Grid &, int,        \
+                                    const double *, const double *, double,   \
+                                    bool, cudaStream_t);
 LBM_DECLARE_PREC(f64)
 LBM_DECLARE_PREC(f32)
 LBM_DECLARE_PREC(bf16)
@@ -98,6 +104,15 @@ LBM_DECLARE_PREC(f16)
 
 inline int tiles_x(int nx) { return (nx + BX - 1) / BX; }
 inline int tiles_y(int ny) { return (ny + BY - 1) / BY; }
+// D3Q15 tiles: 32 x 4 x 2 nodes
+inline int tiles3_x(int nx) { return (nx + 31) / 32; }
+inline int tiles3_y(int ny) { return (ny + 3) / 4; }
+inline int tiles3_z(int nz) { return (nz + 1) / 2; }
+// CTAs of the generic step / moments / diagnostics kernel of a grid
+inline size_t tiles_total(int lattice, int nx, int ny, int nz) {
+  return lattice == 1 ? (size_t)tiles3_x(nx) * tiles3_y(ny) * tiles3_z(nz)
+                      : (size_t)tiles_x(nx) * tiles_y(ny);
+}
 
 }  // namespace lbm
 

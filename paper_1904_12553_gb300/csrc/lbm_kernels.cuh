@@ -108,7 +108,7 @@ template <int P> struct KArgs {
   double *o_phi, *o_c, *o_u, *o_p, *o_rho, *red;
   int *err;
   int mode;
-  T lam[4][4], bulk, a[4], tau_inv[4], src[4], tg_inv, ffac, jfac, grav[2];
+  T lam[4][4], bulk, a[4], tau_inv[4], src[4], tg_inv, ffac, jfac, grav[2], grav_z;
   T off[4], mul[4], c0[5], Q[5][4], rho_base, K[4], kap[4], kmob[4];
   T sh_ld, sh_st, sg_ld, sg_st;  // 16-bit storage: value = S * w_k * ld
 };
@@ -160,6 +160,7 @@ KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
   a.jfac = (T)c.jfac;
   a.grav[0] = (T)c.grav[0];
   a.grav[1] = (T)c.grav[1];
+  a.grav_z = (T)c.grav[2];
   a.rho_base = (T)c.rho_base;
   a.sh_ld = (T)(1.0 / c.sh);
   a.sh_st = (T)c.sh;
@@ -1192,6 +1193,8 @@ cudaError_t launch_init_p(const Consts &c, const Grid &g, int cur,
 
 }  // namespace lbm
 
+#include "lbm_d3q15.cuh"
+
 #define LBM_DEFINE_PREC(SUFFIX, P)                                             \
   namespace lbm {                                                              \
   cudaError_t launch_tile_##SUFFIX(const Consts &c, const Grid &g, int cur,    \
@@ -1206,5 +1209,15 @@ cudaError_t launch_init_p(const Consts &c, const Grid &g, int cur,
   }                                                                            \
   bool encode_tma_##SUFFIX(const Consts &c, Grid &g, EncodeTiledFn enc) {      \
     return encode_tma_p<P>(c, g, enc);                                         \
+  }                                                                            \
+  cudaError_t launch_tile3_##SUFFIX(const Consts &c, const Grid &g, int cur,   \
+                                    int mode, const Outputs &o, bool nonunif,  \
+                                    bool wall, cudaStream_t s) {               \
+    return launch_tile3_p<P>(c, g, cur, mode, o, nonunif, wall, s);            \
+  }                                                                            \
+  cudaError_t launch_init3_##SUFFIX(const Consts &c, const Grid &g, int cur,   \
+                                    const double *cin, const double *uin,      \
+                                    double p0, bool wall, cudaStream_t s) {    \
+    return launch_init3_p<P>(c, g, cur, cin, uin, p0, wall, s);                \
   }                                                                            \
   }

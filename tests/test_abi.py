@@ -109,6 +109,25 @@ def test_invalid_parameters_rejected(lib, bad):
     assert P.lbm_nphase_workspace_bytes(p) == 0
 
 
+@pytest.mark.parametrize("bad", [
+    dict(lattice=2), dict(lattice=1, nz=0), dict(lattice=0, nz=3),
+    dict(lattice=1, nz=4, grad_scheme=1), dict(gravity=[0.0, 0.0, 1e-5]),
+])
+def test_invalid_lattice_parameters_rejected(lib, bad):
+    p = {**W.static_drops().params, **bad}
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_nphase_derive(p)
+    assert e.value.status == 1
+
+
+def test_d3q15_workspace(lib):
+    p3 = W.base_params3(3, 16, 12, 10, 1e-3, precision="fp32")
+    b = P.lbm_nphase_workspace_bytes(p3)
+    V = 16 * 12 * 10
+    # 2 x (2 rest + 2 x 14 moving + 14 NS + 2 phi_prev) + 3 u_prev floats
+    assert b >= (2 * (2 + 28 + 14 + 2) + 3) * V * 4
+
+
 def test_indefinite_lambda_rejected(lib):
     """N = 4 with sigma_13 = 2e-3 and the other pairs 1e-3 gives a lambda of
     Eq. N14 with a negative eigenvalue: the gradient energy of Eq. N11 is

@@ -1,0 +1,143 @@
+"""D3Q15 (three-dimensional) GPU path against the 3-D FP64 oracle, and its
+physics: a sphere's pressure jump 2 sigma / R."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_12553_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_12553_gb300 import build
+    build.build()
+
+
+def _accept(rho=None):
+    def ok(sig):
+        ev = np.linalg.eigvalsh(oracle.lam(W.base_params(sig.shape[0], 4, 4, sig, rho=rho)))
+        return ev[0] > 1e-3 * ev[-1]
+    return ok
+
+
+def gpu3(w, steps, prec=None):
+    from paper_1904_12553_gb300 import Solver
+    s = Solver({**w.params, **({"precision": prec} if prec else {})})
+    s.init(w.c0, w.u0)
+    s.step(steps)
+    m = s.moments()
+    s.close()
+    return m
+
+
+def md(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max())
+
+
+CASES = [(N, shape, wall, nu)
+         for N in (2, 3, 5)
+         for shape in ((10, 9, 8), (37, 13, 5), (3, 4, 2))
+         for wall in (0, 1)
+         for nu in (False, True)]
+
+
+@pytest.mark.parametrize("N,shape,wall,nu", CASES)
+def test_d3q15_fp64_short_runs(N, shape, wall, nu):
+    nx, ny, nz = shape
+    seed = 100 * N + nx + ny + nz + 7 * wall + int(nu)
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.5, 8.0, N) if nu else None
+    w = W.random_smooth3(seed, N, nx, ny, nz, rho=rho, wall_y=wall, amp_u=0.02,
+                         gravity=(1e-5, -2e-5, 3e-5) if nu else (0.0, 0.0, 0.0),
+                         sigma=W.sample_sigma(rng, N, accept=_accept(rho)))
+    for steps in (1, 10):
+        g = gpu3(w, steps)
+        o = oracle.run3(w.params, w.c0, w.u0, steps=steps)
+        assert md(g["phi"], o["phi"]) <= 1e-12
+        assert md(g["u"], o["u"]) <= 1e-13
+        assert md(g["p"], o["p"]) <= 1e-12
+        assert md(g["c"], o["c"]) <= 1e-11
+
+
+def test_d3q15_spheres_fp64_200_steps():
+    w = W.sphere_drops3(n=24, N=3, R=5.0, precision="fp64")
+    g = gpu3(w, 200)
+    o = oracle.run3(w.params, w.c0, steps=200)
+    assert md(g["phi"], o["phi"]) <= 1e-10
+    assert md(g["u"], o["u"]) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_d3q15_precision_forms(prec):
+    w = W.sphere_drops3(n=24, N=3, R=5.0, precision="fp64")
+    o = oracle.run3(w.params, w.c0, steps=200)
+    g = gpu3(w, 200, prec=prec)
+    assert md(g["phi"], o["phi"]) <= 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_d3q15_quiescent_exact(prec):
+    N, sh = 4, (6, 9, 40)
+    c = np.broadcast_to(np.array([0.1, 0.2, 0.3, 0.4])[:, None, None, None],
+                        (N,) + sh).copy()
+    p = W.base_params3(N, sh[2], sh[1], sh[0], 1e-3, rho=[2, 1, 3, 7],
+                       precision=prec, wall_y=1)
+    w = W.Workload("q3", p, c)
+    g = gpu3(w, 300)
+    assert np.abs(g["u"]).max() == 0.0
+    assert np.ptp(g["phi"], axis=(1, 2, 3)).max() == 0.0
+
+
+def test_d3q15_diagnostics_and_resume():
+    from paper_1904_12553_gb300 import Solver
+    w = W.random_smooth3(7, 3, 34, 9, 6, amp_u=0.02, precision="fp32",
+                         sigma=W.sample_sigma(np.random.default_rng(7), 3,
+                                              accept=_accept()))
+    a = Solver(w.params)
+    a.init(w.c0, w.u0)
+    m0, _, _ = a.diagnostics()
+    a.step(9)
+    blob = a.get_state()
+    a.step(11)
+    m1, ke, _ = a.diagnostics()
+    ref = a.moments()
+    # each diagnostic sums phi rounded to FP32 (~sqrt(V) 3e-8 per sum)
+    np.testing.assert_allclose(m1, m0, rtol=1e-7)
+    np.testing.assert_allclose(m1, ref["c"].sum((1, 2, 3)), rtol=1e-12)
+    b = Solver(w.params)
+    b.set_state(blob)
+    b.step(11)
+    got = b.moments()
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    a.close()
+    b.close()
+
+
+def test_sphere_laplace_3d():
+    """Sphere of phase 2 (R = 10) in phase 1 on 48^3: the pressure jump is
+    2 sigma / R in three dimensions (within 6% at W = 4)."""
+    from paper_1904_12553_gb300 import Solver
+    n, R, sig = 48, 10.0, 1e-3
+    c = np.zeros((3, n, n, n))
+    c[1] = W.sphere(n, n, n, n / 2, n / 2, n / 2, R)
+    c[0] = 1.0 - c[1]
+    p = W.base_params3(3, n, n, n, sig, precision="fp32")
+    s = Solver(p)
+    s.init(c)
+    s.step(8000)
+    m = s.moments()
+    s.close()
+    z, y, x = np.mgrid[0:n, 0:n, 0:n]
+    r = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - n / 2) ** 2)
+    dp = m["p"][r < R / 2].mean() - m["p"][(m["c"][0] > 0.999) & (r > R + 8)].mean()
+    print(f"\nsphere R={R}: dp={dp:.4e} 2 sigma/R={2 * sig / R:.4e} "
+          f"ratio={dp / (2 * sig / R):.4f}")
+    assert abs(dp / (2 * sig / R) - 1) <= 0.06
