@@ -886,10 +886,22 @@ __global__ void __launch_bounds__(NT, 1)
         if (err) err[i] = e;
       }
     };
-    // own node (ly = ty + 1, lx = tx + 1; box column tx + HX, row ty + 1)
-    T perr[NP];
+    // own node (ly = ty + 1, lx = tx + 1; box column tx + HX, row ty + 1):
+    // its populations go to registers once, for phi and for the collision.
+    T perr[NP], hreg[NP][9], g[9], pp[NP];
     if (active) {
-      box_phi(tx + G::HXM, tx + G::HXR, ty + 1, perr);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        hreg[i][0] = sh0[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
+#pragma unroll
+        for (int k = 1; k < 9; ++k)
+          hreg[i][k] = to_T(shm[((i * 8 + k - 1) * G::HB + ty + 1) * G::WM + tx + G::HXM]);
+        pp[i] = spp[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
+        sphi[i * PL + (ty + 1) * SW + tx + 1] =
+            node_phi<P>(hreg[i][0], &hreg[i][1], pp[i], perr[i], a.sh_ld);
+      }
+#pragma unroll
+      for (int k = 1; k < 9; ++k) g[k] = to_T(sgm[((k - 1) * BY + ty) * BX + tx]);
     } else {
       phi_global<P, NP>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                         (ty + 1) * SW + tx + 1);
@@ -920,17 +932,6 @@ __global__ void __launch_bounds__(NT, 1)
     }
 
     if (active) {
-      T hreg[NP][9], g[9], pp[NP];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        hreg[i][0] = sh0[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
-#pragma unroll
-        for (int k = 1; k < 9; ++k)
-          hreg[i][k] = to_T(shm[((i * 8 + k - 1) * G::HB + ty + 1) * G::WM + tx + G::HXM]);
-        pp[i] = spp[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
-      }
-#pragma unroll
-      for (int k = 1; k < 9; ++k) g[k] = to_T(sgm[((k - 1) * BY + ty) * BX + tx]);
       NodeMac<P, NP> m;
       node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1,
                                        0, 0, g, m);
