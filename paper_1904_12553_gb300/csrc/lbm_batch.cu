@@ -29,22 +29,6 @@ template <int P> struct BatchCase {
   int np, wall, ntx, nty;
 };
 
-// Ring entry r of a (BX + 2) x (TBY + 2) tile: top row, bottom row, left
-// column, right column.
-template <int TBY>
-__device__ __forceinline__ void ring_pos_1(int r, int &lx, int &ly) {
-  constexpr int SW = BX + 2;
-  if (r < SW) {
-    ly = 0; lx = r;
-  } else if (r < 2 * SW) {
-    ly = TBY + 1; lx = r - SW;
-  } else if (r < 2 * SW + TBY) {
-    ly = 1 + (r - 2 * SW); lx = 0;
-  } else {
-    ly = 1 + (r - 2 * SW - TBY); lx = BX + 1;
-  }
-}
-
 // One time step of one BX x TBY tile of one case (equal densities).
 template <int P, int NP, bool WALL, int TBY>
 __device__ __forceinline__ void tile_step_body(const KArgs<P> &a, int x0, int y0,

@@ -728,6 +728,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 //    loaded directly, one barrier per tile (stage j-1 refilled after the phi
 //    barrier of tile j, phi tile double-buffered). 3 stages with one CTA per
 //    SM: 6% slower; 4 stages: 12% slower.
+//  - Tile height 8: FP32 with 32 x 12 tiles (384 threads, 225 KB) ran 30%
+//    slower; a stage without halo columns (wrapped ring columns from global
+//    memory, two CTAs per SM) ran 48% slower.
 template <int P> struct TmaGeom {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
@@ -735,8 +738,10 @@ template <int P> struct TmaGeom {
   static constexpr int HXR = 16 / (int)sizeof(T);   // halo columns, FP32 planes
   static constexpr int WM = BX + 2 * HXM;           // box widths
   static constexpr int WR = BX + 2 * HXR;
-  static constexpr int HB = BY + 2;                 // box height
   static constexpr bool WIDE = sizeof(Sm) == 4;     // FP32 storage
+  static constexpr int TBY = 8;                     // tile height
+  static constexpr int NTH = BX * TBY;              // threads per CTA
+  static constexpr int HB = TBY + 2;                // box height
   static constexpr int S = 2;                       // pipeline stages
   static constexpr bool STAGE_U = WIDE;             // u(t-1) in the stage
   static constexpr bool TWO_BARRIERS = WIDE;
@@ -792,23 +797,39 @@ template <int P, int NP> struct TmaStage {
   static constexpr size_t HM = al((size_t)8 * NP * G::HB * G::WM * sizeof(Sm));
   static constexpr size_t H0 = al((size_t)NP * G::HB * G::WR * sizeof(T));
   static constexpr size_t PP = H0;
-  static constexpr size_t GM = al((size_t)8 * BY * BX * sizeof(Sm));
-  static constexpr size_t UP = G::STAGE_U ? al((size_t)2 * BY * BX * sizeof(T)) : 0;
+  static constexpr size_t GM = al((size_t)8 * G::TBY * BX * sizeof(Sm));
+  static constexpr size_t UP = G::STAGE_U ? al((size_t)2 * G::TBY * BX * sizeof(T)) : 0;
   static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
   // bytes the TMA engine writes per stage (full boxes, including fill)
   static constexpr uint32_t TX =
       (uint32_t)((size_t)8 * NP * G::HB * G::WM * sizeof(Sm) +
                  2 * (size_t)NP * G::HB * G::WR * sizeof(T) +
-                 (size_t)8 * BY * BX * sizeof(Sm) +
-                 (G::STAGE_U ? (size_t)2 * BY * BX * sizeof(T) : 0));
-  static constexpr size_t SPHI = al((size_t)NP * (BY + 2) * (BX + 2) * sizeof(T));
+                 (size_t)8 * G::TBY * BX * sizeof(Sm) +
+                 (G::STAGE_U ? (size_t)2 * G::TBY * BX * sizeof(T) : 0));
+  static constexpr size_t SPHI = al((size_t)NP * (G::TBY + 2) * (BX + 2) * sizeof(T));
   static constexpr int S = G::S;
   static constexpr size_t SMEM = S * BYTES + 2 * SPHI + 64;
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
+// Ring entry r of a (BX + 2) x (TBY + 2) tile: top row, bottom row, left
+// column, right column.
+template <int TBY>
+__device__ __forceinline__ void ring_pos_1(int r, int &lx, int &ly) {
+  constexpr int SW = BX + 2;
+  if (r < SW) {
+    ly = 0; lx = r;
+  } else if (r < 2 * SW) {
+    ly = TBY + 1; lx = r - SW;
+  } else if (r < 2 * SW + TBY) {
+    ly = 1 + (r - 2 * SW); lx = 0;
+  } else {
+    ly = 1 + (r - 2 * SW - TBY); lx = BX + 1;
+  }
+}
+
 template <int P, int NP, bool WALL>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
     tile_kernel_tma(const KArgs<P> a, const __grid_constant__ TmaMaps maps,
                     int ntx, int ntiles) {
   typedef typename Prec<P>::T T;
@@ -816,7 +837,8 @@ __global__ void __launch_bounds__(NT, 1)
   typedef TmaGeom<P> G;
   typedef TmaStage<P, NP> St;
   constexpr int S = St::S;
-  constexpr int SW = BX + 2, SH = BY + 2, PL = SW * SH;
+  constexpr int TBY = G::TBY;
+  constexpr int SW = BX + 2, SH = TBY + 2, PL = SW * SH;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + 2 * St::SPHI);
 
@@ -826,7 +848,7 @@ __global__ void __launch_bounds__(NT, 1)
 
   auto issue = [&](int j) {  // thread 0: TMA loads of my j-th tile
     const int t = blockIdx.x + j * gridDim.x;
-    const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
+    const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
     unsigned char *st = smem + (j % S) * St::BYTES;
     uint64_t *b = bar + (j % S);
     mbar_expect_tx(b, St::TX);
@@ -849,7 +871,7 @@ __global__ void __launch_bounds__(NT, 1)
   int failed_at = -1;
   for (int j = 0; j < nmine; ++j) {
     const int t = blockIdx.x + j * gridDim.x;
-    const int x0 = (t % ntx) * BX, y0 = (t / ntx) * BY;
+    const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
     T *sphi = (T *)(smem + S * St::BYTES + (j & 1) * St::SPHI);
     const unsigned char *st = smem + (j % S) * St::BYTES;
     const Sm *shm = (const Sm *)st;
@@ -901,15 +923,16 @@ __global__ void __launch_bounds__(NT, 1)
             node_phi<P>(hreg[i][0], &hreg[i][1], pp[i], perr[i], a.sh_ld);
       }
 #pragma unroll
-      for (int k = 1; k < 9; ++k) g[k] = to_T(sgm[((k - 1) * BY + ty) * BX + tx]);
+      for (int k = 1; k < 9; ++k) g[k] = to_T(sgm[((k - 1) * TBY + ty) * BX + tx]);
     } else {
       phi_global<P, NP>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                         (ty + 1) * SW + tx + 1);
     }
-    constexpr int NRING = SW * SH - BX * BY;
+    constexpr int NRING = SW * SH - BX * TBY;
+    static_assert(NRING <= G::NTH, "one ring position per thread");
     if (tid < NRING) {
       int lx, ly;
-      ring_pos<1>(tid, lx, ly);
+      ring_pos_1<TBY>(tid, lx, ly);
       const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
       if (rx >= 0 && rx < nx && ry >= 0 && ry < ny)
         box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, ly, nullptr);
@@ -938,7 +961,7 @@ __global__ void __launch_bounds__(NT, 1)
       collide_stream<P, NP, false, WALL>(
           a, m, hreg, perr, g, pp,
           G::STAGE_U ? sup[ty * BX + tx] : upx,
-          G::STAGE_U ? sup[(BY + ty) * BX + tx] : upy, gx, gy);
+          G::STAGE_U ? sup[(TBY + ty) * BX + tx] : upy, gx, gy);
     }
     if (G::TWO_BARRIERS) {
       __syncthreads();
@@ -1073,15 +1096,16 @@ cudaError_t launch_tile_t(const Consts &c, const Grid &g, int cur, int mode,
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, tile_kernel_tma<P, NP, WALL>, NT, St::SMEM);
+            &per_sm, tile_kernel_tma<P, NP, WALL>, TmaGeom<P>::NTH, St::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         max_ctas = (per_sm > 0 ? per_sm : 1) * sms;
       }
-      const int ntx = tiles_x(g.nx), ntiles = ntx * tiles_y(g.ny);
+      constexpr int TBY = TmaGeom<P>::TBY;
+      const int ntx = tiles_x(g.nx), ntiles = ntx * ((g.ny + TBY - 1) / TBY);
       const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-      tile_kernel_tma<P, NP, WALL><<<grid, dim3(BX, BY), St::SMEM, s>>>(
+      tile_kernel_tma<P, NP, WALL><<<grid, dim3(BX, TBY), St::SMEM, s>>>(
           a, *(const TmaMaps *)&g.tma[cur], ntx, ntiles);
       return cudaGetLastError();
     }
@@ -1150,8 +1174,8 @@ bool encode_tma_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
       bool ok = enc3(&m.hm, g.hm[b], sizeof(Sm), 8 * NP, G::WM, G::HB, 8 * NP) &&
                 enc3(&m.h0, g.h0[b], sizeof(T), NP, G::WR, G::HB, NP) &&
                 enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HB, NP) &&
-                enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, BY, 8) &&
-                enc3(&m.up, g.u_prev, sizeof(T), 2, BX, BY, 2);
+                enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, G::TBY, 8) &&
+                enc3(&m.up, g.u_prev, sizeof(T), 2, BX, G::TBY, 2);
       if (!ok) return false;
     }
     return true;
