@@ -44,6 +44,16 @@ def alg_bytes_per_node(N: int, prec: str) -> int:
     return 2 * (8 * N * s_mov + (N - 1) * s_rest + (N + 1) * s_rest)
 
 
+# FP64 operations one node-step executes in the FP64 form at N=5 (ncu
+# instruction counts of the step kernel on the 1024x1024 droplets and
+# interfaces case, per node: 226 DFMA counted twice, 171.5 DADD, 132 DMUL;
+# profiles/tile_kernel_fp64_n5_1024.md).
+FP64_FLOP_PER_NODE_N5 = 755.5
+# FP64 ALU peak derived from the GB300's unit counts and clock: 152 SMs x
+# 2 FP64 FMA lanes per SM per clock x 2 FLOP x 2070 MHz = 1.2586 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -305,8 +315,13 @@ def batch_run(steps=50, ncases=256):
     ms_1 = e0.elapsed_time(e1)
     for s in solvers:
         s.close()
+    bytes_step = sum(alg_bytes_per_node(w.params["N"], "fp32") * w.V
+                     for w in cases)
+    peak, _ = peaks()
     return {"cases": ncases, "nodes": nodes, "steps": steps,
             "batched_mlups": nodes * steps / (ms_b / 1e3) / 1e6,
+            "batched_hbm_frac": bytes_step * steps / (ms_b / 1e3) / 1e9 / peak,
+            "alg_bytes_per_step": bytes_step,
             "one_by_one_mlups": nodes * steps / (ms_1 / 1e3) / 1e6,
             "batched_ms_per_step": ms_b / steps,
             "one_by_one_ms_per_step": ms_1 / steps,
@@ -395,6 +410,14 @@ def run_ours(args, dist, rank, world):
                 "mlups": V / (fstep / 1e3) / 1e6, "ms_per_step": fstep,
                 "alg_bytes_per_node": fB, "kernel": fkernel,
                 "hbm_frac": fB * V / (fstep / 1e3) / 1e9 / peak}
+            if prec == "fp64" and N == 5:
+                tf = FP64_FLOP_PER_NODE_N5 * V / (fstep / 1e3) / 1e12
+                forms[prec]["roofline"] = {
+                    "bound": "alu", "achieved": tf, "unit": "TFLOP/s",
+                    "peak": FP64_PEAK_TFLOPS, "frac": tf / FP64_PEAK_TFLOPS,
+                    "flop_per_node": FP64_FLOP_PER_NODE_N5,
+                    "peak_kind": "derived (152 SMs x 2 FP64 FMA/clk x "
+                                 "2070 MHz)"}
     if not args.quick:
         forms["batch"] = batch_run()
         forms["d3q15_fp32"] = d3q15_run()
@@ -426,6 +449,29 @@ def run_ours(args, dist, rank, world):
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+
+
+def run_only(args):
+    """One form alone (for profiler captures): N=5 droplets and interfaces
+    at side --n (2-D forms), the ensemble, or an --n^3 D3Q15 box."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1904_12553_gb300 import build
+    build.build()
+    if args.only == "batch":
+        out = batch_run(steps=args.steps)
+    elif args.only == "d3q15":
+        out = d3q15_run(n=args.n if args.n != 2048 else 128, steps=args.steps)
+    else:
+        w = make_workload(args.only, n=args.n, accept=accept_sigma())
+        ms, _, _, _, kernel = time_form(w, args.only, args.steps, args.warmup)
+        B = alg_bytes_per_node(5, args.only)
+        peak, _ = peaks()
+        step = ms / args.steps
+        out = {"form": args.only, "nx": args.n, "kernel": kernel,
+               "mlups": w.V / (step / 1e3) / 1e6, "ms_per_step": step,
+               "hbm_frac": B * w.V / (step / 1e3) / 1e9 / peak}
+    print(json.dumps(out), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -497,6 +543,10 @@ def main():
                     help="skip the other storage forms and the CPU baseline")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the FP32 step kernel only (profiling runs)")
+    ap.add_argument("--only", default=None,
+                    choices=["fp32", "bf16", "fp16", "fp64", "batch", "d3q15"],
+                    help="time one form alone and print its line "
+                         "(profiling captures)")
     ap.add_argument("--n", type=int, default=2048,
                     help="grid side (2048 is the benchmark workload; smaller "
                          "sides are for profiling captures)")
@@ -513,6 +563,9 @@ def main():
         import torch.distributed as dist_
         dist_.init_process_group("nccl")
         dist = dist_
+    if args.only:
+        run_only(args)
+        return
     try:
         run_ours(args, dist, rank, world)
     finally:

@@ -37,7 +37,8 @@ class Workload:
 
     @property
     def V(self) -> int:
-        return int(self.params["nx"]) * int(self.params["ny"])
+        return (int(self.params["nx"]) * int(self.params["ny"])
+                * int(self.params.get("nz", 1)))
 
 
 def base_params(N: int, nx: int, ny: int, sigma, *, rho=None, tau=0.8,
