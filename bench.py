@@ -327,7 +327,9 @@ def batch_run(steps=50, ncases=256):
             "one_by_one_ms_per_step": ms_1 / steps,
             "schedule": {"tile_height": sched["tile_height"],
                          "schedule": Batch.SCHEDULES[sched["schedule"]],
-                         "ctas": sched["ctas"]},
+                         "ctas": sched["ctas"], "chunk": sched["chunk"],
+                         "kernel": ("pipelined (TMA)" if sched["pipelined"]
+                                    else "generic tile")},
             "kernel_launches_per_step": {"batched": 1,
                                          "one_by_one": ncases}}
 

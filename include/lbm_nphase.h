@@ -188,6 +188,14 @@ typedef struct {
                           cost-ordered list; 1: per-CTA contiguous runs of
                           equal cost; 2: items taken from an atomic counter */
   int32_t ctas;        /* persistent CTAs (0: all that are resident) */
+  int32_t pipelined;   /* 1: TMA-pipelined tile body (32 x 8 tiles, the next
+                          item's populations loaded while the current one is
+                          computed; tile_height is then 8); needs every case
+                          to satisfy the pipelined kernel's conditions
+                          (nx a multiple of 8, lbm_nphase_uses_pipelined_kernel
+                          true for it), else LBM_EINVAL */
+  int32_t chunk;       /* dynamic schedule: consecutive items taken per
+                          atomic grab (0 means 1); ignored otherwise */
 } lbm_nphase_batch_schedule;
 
 /* Workspace for `ncases` grids described by params[0..ncases-1] (0 if a
@@ -197,7 +205,7 @@ size_t lbm_nphase_batch_workspace_bytes(const lbm_nphase_params *params,
 
 /* Create the batch in caller-owned device memory (256-byte aligned) on the
  * current device; work is ordered on `cuda_stream`. The initial schedule is
- * {8, 2, 0}. Errors as lbm_nphase_create. */
+ * {8, 2, 0, 0, 1}. Errors as lbm_nphase_create. */
 lbm_status lbm_nphase_batch_create(const lbm_nphase_params *params, int ncases,
                                    void *d_workspace, size_t workspace_bytes,
                                    void *cuda_stream, lbm_nphase_batch_t **out);
@@ -217,10 +225,13 @@ lbm_status lbm_nphase_batch_step(lbm_nphase_batch_t *b, int64_t nsteps);
  * then returns LBM_ESTATE until the case is re-initialised). */
 lbm_nphase_t *lbm_nphase_batch_case(lbm_nphase_batch_t *b, int c);
 
-/* Time every tile height x schedule (with all resident CTAs) over
+/* Time every kernel variant (generic at tile heights 4 and 8, and the
+ * pipelined kernel when every case allows it) x schedule (strided, lists,
+ * dynamic with chunks of 1, 4 and 16), with all resident CTAs, over
  * 2 * trial_steps steps each and keep the fastest; its time per step goes to
  * *best_ms_per_step (may be NULL). The trials advance the cases' state by
- * 12 * (trial_steps + 1) steps: re-initialise afterwards for a clean run. */
+ * 2 * (trial_steps + 1) steps per candidate (10 or 15 candidates):
+ * re-initialise afterwards for a clean run. */
 lbm_status lbm_nphase_batch_autotune(lbm_nphase_batch_t *b, int trial_steps,
                                      double *best_ms_per_step);
 

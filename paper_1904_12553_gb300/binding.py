@@ -57,7 +57,8 @@ class LbmModel(C.Structure):
 
 class LbmSchedule(C.Structure):
     _fields_ = [("tile_height", C.c_int32), ("schedule", C.c_int32),
-                ("ctas", C.c_int32)]
+                ("ctas", C.c_int32), ("pipelined", C.c_int32),
+                ("chunk", C.c_int32)]
 
 
 _LIB = None
@@ -423,8 +424,9 @@ def lbm_nphase_batch_autotune(batch: int, trial_steps: int) -> float:
 
 
 def lbm_nphase_batch_set_schedule(batch: int, tile_height: int, schedule: int,
-                                  ctas: int = 0):
-    s = LbmSchedule(tile_height, schedule, ctas)
+                                  ctas: int = 0, pipelined: int = 0,
+                                  chunk: int = 1):
+    s = LbmSchedule(tile_height, schedule, ctas, pipelined, chunk)
     _check(load_library().lbm_nphase_batch_set_schedule(C.c_void_p(batch),
                                                         C.byref(s)),
            "lbm_nphase_batch_set_schedule")
@@ -436,7 +438,7 @@ def lbm_nphase_batch_get_schedule(batch: int) -> dict:
                                                         C.byref(s)),
            "lbm_nphase_batch_get_schedule")
     return {"tile_height": s.tile_height, "schedule": s.schedule,
-            "ctas": s.ctas}
+            "ctas": s.ctas, "pipelined": s.pipelined, "chunk": s.chunk}
 
 
 def lbm_nphase_batch_destroy(batch: int):
@@ -496,8 +498,10 @@ class Batch:
     def autotune(self, trial_steps: int = 3) -> float:
         return lbm_nphase_batch_autotune(self.handle, trial_steps)
 
-    def set_schedule(self, tile_height: int, schedule: int, ctas: int = 0):
-        lbm_nphase_batch_set_schedule(self.handle, tile_height, schedule, ctas)
+    def set_schedule(self, tile_height: int, schedule: int, ctas: int = 0,
+                     pipelined: bool = False, chunk: int = 1):
+        lbm_nphase_batch_set_schedule(self.handle, tile_height, schedule, ctas,
+                                      int(pipelined), chunk)
 
     def schedule(self) -> dict:
         return lbm_nphase_batch_get_schedule(self.handle)

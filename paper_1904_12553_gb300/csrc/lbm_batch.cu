@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(BX *TBY)
     batch_kernel(const BatchCase<P> *__restrict__ cases,
                  const int2 *__restrict__ items, int nitems,
                  const int *__restrict__ list_off, const int *__restrict__ list,
-                 int sched, int *counter, int cur) {
+                 int sched, int chunk, int *counter, int cur) {
   typedef typename Prec<P>::T T;
   constexpr int SW = BX + 2, SH = TBY + 2;
   __shared__ KArgs<P> sa;
@@ -93,13 +93,19 @@ __global__ void __launch_bounds__(BX *TBY)
   __shared__ int s_item, s_np, s_wall, s_ntx;
   const int tid = threadIdx.y * BX + threadIdx.x;
   int loaded = -1;
-  int k = 0;
+  int k = 0, cbase = 0, cleft = 0;  // dynamic: current chunk (thread 0)
   const int lbeg = sched == SCHED_LISTS ? list_off[blockIdx.x] : 0;
   const int lend = sched == SCHED_LISTS ? list_off[blockIdx.x + 1] : 0;
   for (;;) {
     int item;
     if (sched == SCHED_DYNAMIC) {
-      if (tid == 0) s_item = atomicAdd(counter, 1);
+      if (tid == 0) {
+        if (cleft == 0) {
+          cbase = atomicAdd(counter, 1) * chunk;
+          cleft = chunk;
+        }
+        s_item = cbase + chunk - cleft--;
+      }
       __syncthreads();
       item = s_item;
       __syncthreads();
@@ -138,6 +144,291 @@ __global__ void __launch_bounds__(BX *TBY)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined batch kernel (FP32 storage, 32 x 8 tiles): the tile body of
+// tile_kernel_tma applied to (case, tile) items, with the boxes of the CTA's
+// next item in flight while the current one is computed. Each stage holds one
+// item's populations and a copy of its case's kernel arguments, all counted
+// on the stage's mbarrier, so a change of case costs no extra barrier.
+// Thread 0 issues the copies; it keeps the next item's descriptor (case,
+// tile origin, N - 1 and walls: precomputed on the host) and the index of
+// the one after it in flight one tile ahead, so that no global load or
+// atomic sits between a finished tile and the next issue. Tensor maps live
+// in global memory (written by the host before the launch) and are acquired
+// through the tensormap proxy when the issuing thread meets a new case. A
+// ring of S slots in shared memory tells the other threads what each stage
+// holds (case -1: the CTA's items are done). Stages are sized for N - 1 = 4
+// and laid out per item for its own N - 1.
+// ---------------------------------------------------------------------------
+typedef TmaGeom<LBM_FP32> BG;
+typedef TmaStage<LBM_FP32, 4> BSt;
+constexpr size_t kArgsBytes = sizeof(KArgs<LBM_FP32>);
+static_assert(kArgsBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+constexpr size_t kStageStride = BSt::BYTES + ((kArgsBytes + 127) & ~(size_t)127);
+constexpr size_t kBatchSmem = BSt::S * kStageStride + 2 * BSt::SPHI + 64;
+static_assert(kBatchSmem <= 232448, "shared memory per CTA");
+
+// Item descriptor of the pipelined kernel.
+struct alignas(16) TmaItem {
+  int c, x0, y0, cls;  // case, tile origin, 2 (N - 1) + walls
+};
+
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(m)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src,
+                                          uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int NP>
+__device__ __forceinline__ void batch_issue_np(unsigned char *st, uint64_t *b,
+                                               const TmaMaps *m,
+                                               const KArgs<LBM_FP32> *args,
+                                               int x0, int y0) {
+  typedef TmaStage<LBM_FP32, NP> St;
+  mbar_expect_tx(b, St::TX + (uint32_t)kArgsBytes);
+  tma_load_3d(st, &m->hm, x0 - BG::HXM, y0 - 1, 0, b);
+  tma_load_3d(st + St::HM, &m->h0, x0 - BG::HXR, y0 - 1, 0, b);
+  tma_load_3d(st + St::HM + St::H0, &m->pp, x0 - BG::HXR, y0 - 1, 0, b);
+  tma_load_3d(st + St::HM + St::H0 + St::PP, &m->gm, x0, y0, 0, b);
+  tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &m->up, x0, y0, 0, b);
+  bulk_load(st + BSt::BYTES, args, (uint32_t)kArgsBytes, b);
+}
+
+// One staged tile in two phases around one CTA barrier: (1) the own node's
+// populations into registers and phi on the tile and its ring, (2)
+// collisions and streaming. The register arrays are sized for N - 1 = 4 and
+// shared by every (N - 1, walls) variant, so that the variants do not add up
+// their live registers across the barrier.
+struct TileRegs {
+  float hreg[4][9], perr[4], pp[4], g[9];
+};
+
+template <int NP, bool WALL>
+__device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
+                                              const unsigned char *st,
+                                              float *sphi, int x0, int y0,
+                                              TileRegs &r) {
+  typedef float T;
+  typedef typename Prec<LBM_FP32>::Sm Sm;
+  typedef TmaStage<LBM_FP32, NP> St;
+  constexpr int TBY = BG::TBY;
+  constexpr int SW = BX + 2, SH = TBY + 2, PL = SW * SH;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int nx = a.nx, ny = a.ny;
+  const Sm *shm = (const Sm *)st;
+  const T *sh0 = (const T *)(st + St::HM);
+  const T *spp = (const T *)(st + St::HM + St::H0);
+  const Sm *sgm = (const Sm *)(st + St::HM + St::H0 + St::PP);
+  const int gx = x0 + tx, gy = y0 + ty;
+  if (gx < nx && gy < ny) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      r.hreg[i][0] = sh0[(i * BG::HB + ty + 1) * BG::WR + tx + BG::HXR];
+#pragma unroll
+      for (int k = 1; k < 9; ++k)
+        r.hreg[i][k] = to_T(shm[((i * 8 + k - 1) * BG::HB + ty + 1) * BG::WM + tx + BG::HXM]);
+      r.pp[i] = spp[(i * BG::HB + ty + 1) * BG::WR + tx + BG::HXR];
+      sphi[i * PL + (ty + 1) * SW + tx + 1] = node_phi<LBM_FP32>(
+          r.hreg[i][0], &r.hreg[i][1], r.pp[i], r.perr[i], a.sh_ld);
+    }
+#pragma unroll
+    for (int k = 1; k < 9; ++k) r.g[k] = to_T(sgm[((k - 1) * TBY + ty) * BX + tx]);
+  } else {
+    phi_global<LBM_FP32, NP>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
+                             (ty + 1) * SW + tx + 1);
+  }
+  constexpr int NRING = SW * SH - BX * TBY;
+  if (tid < NRING) {
+    int lx, ly;
+    ring_pos_1<TBY>(tid, lx, ly);
+    const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
+    if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) {
+      const int bxm = lx - 1 + BG::HXM, bxr = lx - 1 + BG::HXR;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T mov[8], e;
+#pragma unroll
+        for (int k = 1; k < 9; ++k)
+          mov[k - 1] = to_T(shm[((i * 8 + k - 1) * BG::HB + ly) * BG::WM + bxm]);
+        sphi[i * PL + ly * SW + lx] = node_phi<LBM_FP32>(
+            sh0[(i * BG::HB + ly) * BG::WR + bxr], mov,
+            spp[(i * BG::HB + ly) * BG::WR + bxr], e, a.sh_ld);
+      }
+    } else {
+      phi_global<LBM_FP32, NP>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
+                               ly * SW + lx);
+    }
+  }
+}
+
+template <int NP, bool WALL>
+__device__ __forceinline__ void batch_tma_collide(const KArgs<LBM_FP32> &a,
+                                                  const unsigned char *st,
+                                                  const float *sphi, int x0,
+                                                  int y0, TileRegs &r) {
+  typedef TmaStage<LBM_FP32, NP> St;
+  constexpr int TBY = BG::TBY;
+  constexpr int SW = BX + 2, PL = SW * (TBY + 2);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int gx = x0 + tx, gy = y0 + ty;
+  if (gx >= a.nx || gy >= a.ny) return;
+  const float *sup = (const float *)(st + St::HM + St::H0 + St::PP + St::GM);
+  float hreg[NP][9], perr[NP], pp[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    perr[i] = r.perr[i];
+    pp[i] = r.pp[i];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) hreg[i][k] = r.hreg[i][k];
+  }
+  NodeMac<LBM_FP32, NP> m;
+  node_macros<LBM_FP32, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1,
+                                          tx + 1, 0, 0, r.g, m);
+  collide_stream<LBM_FP32, NP, false, WALL>(a, m, hreg, perr, r.g, pp,
+                                            sup[ty * BX + tx],
+                                            sup[(TBY + ty) * BX + tx], gx, gy);
+}
+
+__global__ void __launch_bounds__(BG::NTH, 1)
+    batch_kernel_tma(const BatchCase<LBM_FP32> *__restrict__ cases,
+                     const TmaMaps *__restrict__ maps, int ncases,
+                     const TmaItem *__restrict__ items, int nitems,
+                     const int *__restrict__ list_off,
+                     const int *__restrict__ list, int sched, int chunk,
+                     int *counter, int cur) {
+  constexpr int S = BSt::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = (uint64_t *)(smem + S * kStageStride + 2 * BSt::SPHI);
+  __shared__ TmaItem s_slot[S];
+  const int tid = threadIdx.y * BX + threadIdx.x;
+
+  // Schedule state (thread 0 only): the CTA's k-th item index, the
+  // descriptor of the next item to issue and the index of the one after.
+  int k = 0, issued = 0, fenced = -1, cbase = 0, cleft = 0;
+  const int lbeg = sched == SCHED_LISTS ? list_off[blockIdx.x] : 0;
+  const int lend = sched == SCHED_LISTS ? list_off[blockIdx.x + 1] : 0;
+  auto next_index = [&]() -> int {
+    int item;
+    if (sched == SCHED_DYNAMIC) {
+      if (cleft == 0) {
+        cbase = atomicAdd(counter, 1) * chunk;
+        cleft = chunk;
+      }
+      item = cbase + chunk - cleft--;
+    }
+    else if (sched == SCHED_LISTS) item = lbeg + k < lend ? list[lbeg + k] : nitems;
+    else item = blockIdx.x + k * gridDim.x;
+    ++k;
+    return item;
+  };
+  const TmaItem none = {-1, 0, 0, 0};
+  TmaItem d_next = none;
+  int i_after = nitems;
+  auto issue = [&](int j) {  // thread 0: the CTA's j-th item into stage j % S
+    const int slot = j % S;
+    const TmaItem d = d_next;
+    if (d.c >= 0) {
+      d_next = i_after < nitems ? items[i_after] : none;
+      i_after = i_after < nitems ? next_index() : nitems;
+    }
+    s_slot[slot] = d;
+    if (d.c < 0) return;
+    const TmaMaps *m = maps + 2 * d.c + cur;
+    if (d.c != fenced) {
+      tensormap_acquire(&m->hm);
+      tensormap_acquire(&m->h0);
+      tensormap_acquire(&m->pp);
+      tensormap_acquire(&m->gm);
+      tensormap_acquire(&m->up);
+      fenced = d.c;
+    }
+    unsigned char *st = smem + slot * kStageStride;
+    const KArgs<LBM_FP32> *args = &cases[d.c].a[cur];
+    switch (d.cls >> 1) {
+      case 1: batch_issue_np<1>(st, bar + slot, m, args, d.x0, d.y0); break;
+      case 2: batch_issue_np<2>(st, bar + slot, m, args, d.x0, d.y0); break;
+      case 3: batch_issue_np<3>(st, bar + slot, m, args, d.x0, d.y0); break;
+      default: batch_issue_np<4>(st, bar + slot, m, args, d.x0, d.y0); break;
+    }
+    ++issued;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(bar + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const int i0 = next_index();
+    if (i0 < nitems) {
+      d_next = items[i0];
+      i_after = next_index();
+    }
+    for (int j = 0; j < S; ++j) issue(j);
+  }
+  __syncthreads();
+
+  int failed_at = -1;
+  for (int j = 0;; ++j) {
+    const int slot = j % S;
+    const TmaItem d = s_slot[slot];
+    if (d.c < 0) break;
+    const bool ok = mbar_wait(bar + slot, (uint32_t)((j / S) & 1));
+    const unsigned char *st = smem + slot * kStageStride;
+    const KArgs<LBM_FP32> &sa = *(const KArgs<LBM_FP32> *)(st + BSt::BYTES);
+    float *sphi = (float *)(smem + S * kStageStride + (j & 1) * BSt::SPHI);
+    const int x0 = d.x0, y0 = d.y0;
+    TileRegs r;
+    switch (d.cls) {
+      case 2: batch_tma_phi<1, false>(sa, st, sphi, x0, y0, r); break;
+      case 3: batch_tma_phi<1, true>(sa, st, sphi, x0, y0, r); break;
+      case 4: batch_tma_phi<2, false>(sa, st, sphi, x0, y0, r); break;
+      case 5: batch_tma_phi<2, true>(sa, st, sphi, x0, y0, r); break;
+      case 6: batch_tma_phi<3, false>(sa, st, sphi, x0, y0, r); break;
+      case 7: batch_tma_phi<3, true>(sa, st, sphi, x0, y0, r); break;
+      case 8: batch_tma_phi<4, false>(sa, st, sphi, x0, y0, r); break;
+      case 9: batch_tma_phi<4, true>(sa, st, sphi, x0, y0, r); break;
+    }
+    // A thread whose wait gave up ran the phi sums on stale shared data
+    // (harmlessly); this barrier makes the decision to stop CTA-wide.
+    if (__syncthreads_or(!ok)) {
+      failed_at = j;
+      break;
+    }
+    switch (d.cls) {
+      case 2: batch_tma_collide<1, false>(sa, st, sphi, x0, y0, r); break;
+      case 3: batch_tma_collide<1, true>(sa, st, sphi, x0, y0, r); break;
+      case 4: batch_tma_collide<2, false>(sa, st, sphi, x0, y0, r); break;
+      case 5: batch_tma_collide<2, true>(sa, st, sphi, x0, y0, r); break;
+      case 6: batch_tma_collide<3, false>(sa, st, sphi, x0, y0, r); break;
+      case 7: batch_tma_collide<3, true>(sa, st, sphi, x0, y0, r); break;
+      case 8: batch_tma_collide<4, false>(sa, st, sphi, x0, y0, r); break;
+      case 9: batch_tma_collide<4, true>(sa, st, sphi, x0, y0, r); break;
+    }
+    // Every thread is done with this stage: refill it.
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(j + S);
+    }
+  }
+  if (failed_at >= 0) {
+    // Every case's state is now suspect: flag all of them, then let the
+    // copies still in flight (items failed_at .. issued-1) land, with the
+    // same bounded wait, before the CTA's shared memory is released.
+    if (tid == 0) {
+      for (int c = 0; c < ncases; ++c) atomicExch(cases[c].a[0].err, 1);
+      for (int j = failed_at; j < issued; ++j)
+        mbar_wait(bar + (j % S), (uint32_t)((j / S) & 1));
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace lbm
 
 // --------------------------------------------------------------------------
@@ -158,12 +449,16 @@ struct lbm_nphase_batch_t {
   cudaStream_t stream;     // caller's stream
   cudaStream_t cap;        // private stream for graph capture
   Case32 *d_cases;         // descriptors (device)
+  lbm::TmaMaps *d_maps;    // tensor maps [case][input buffer] (device)
+  bool tma_ok;             // every case has tensor maps (pipelined kernel)
   int2 *d_items;           // (case, tile) items (device)
+  lbm::TmaItem *d_titems;  // the same items for the pipelined kernel
   int *d_list_off, *d_list, *d_counter;
   size_t items_cap, lists_cap;
   int nitems;
   lbm_nphase_batch_schedule sched;
-  int max_ctas[2];         // resident CTAs per tile height
+  int max_ctas[2];         // resident CTAs per tile height (generic kernel)
+  int max_ctas_tma;        // resident CTAs of the pipelined kernel
   cudaGraphExec_t exec[2]; // two steps starting at buffer 0 / 1
   int cur;
   int64_t steps;
@@ -200,25 +495,34 @@ cudaError_t launch_once(lbm_nphase_batch_t *b, cudaStream_t s, int cur) {
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
   }
-  if (ti == 0)
+  if (b->sched.pipelined)
+    lbm::batch_kernel_tma<<<grid, dim3(lbm::BX, lbm::BG::TBY), lbm::kBatchSmem, s>>>(
+        b->d_cases, b->d_maps, b->n, b->d_titems, b->nitems, b->d_list_off,
+        b->d_list, b->sched.schedule, b->sched.chunk, b->d_counter, cur);
+  else if (ti == 0)
     lbm::batch_kernel<LBM_FP32, 4><<<grid, dim3(lbm::BX, 4), 0, s>>>(
         b->d_cases, b->d_items, b->nitems, b->d_list_off, b->d_list,
-        b->sched.schedule, b->d_counter, cur);
+        b->sched.schedule, b->sched.chunk, b->d_counter, cur);
   else
     lbm::batch_kernel<LBM_FP32, 8><<<grid, dim3(lbm::BX, 8), 0, s>>>(
         b->d_cases, b->d_items, b->nitems, b->d_list_off, b->d_list,
-        b->sched.schedule, b->d_counter, cur);
+        b->sched.schedule, b->sched.chunk, b->d_counter, cur);
   return cudaGetLastError();
 }
 
 // Work items and schedules for one tile height and CTA count.
 lbm_status build_schedule(lbm_nphase_batch_t *b, lbm_nphase_batch_schedule s) {
+  if (s.pipelined != 0 && s.pipelined != 1) return LBM_EINVAL;
+  if (s.pipelined && !b->tma_ok) return LBM_EINVAL;
+  if (s.pipelined) s.tile_height = lbm::BG::TBY;
   const int tby = s.tile_height;
   const int ti = tby == 4 ? 0 : 1;
   if (tby != 4 && tby != 8) return LBM_EINVAL;
   if (s.schedule < 0 || s.schedule > 2) return LBM_EINVAL;
-  if (s.ctas <= 0) s.ctas = b->max_ctas[ti];
-  if (s.ctas > b->max_ctas[ti]) s.ctas = b->max_ctas[ti];
+  const int cap = s.pipelined ? b->max_ctas_tma : b->max_ctas[ti];
+  if (s.chunk < 0) return LBM_EINVAL;
+  if (s.chunk == 0) s.chunk = 1;
+  if (s.ctas <= 0 || s.ctas > cap) s.ctas = cap;
   // Cases in order of decreasing work (cost of a tile ~ N), tiles of a case
   // consecutive (neighbouring tiles share halos in L2).
   std::vector<int> order(b->n);
@@ -262,6 +566,20 @@ lbm_status build_schedule(lbm_nphase_batch_t *b, lbm_nphase_batch_schedule s) {
   cudaError_t e;
   e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2),
                       cudaMemcpyHostToDevice, b->stream);
+  std::vector<lbm::TmaItem> titems;
+  if (s.pipelined) {
+    titems.resize(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+      const lbm_nphase_t *h = b->cases[items[i].x];
+      const int ntx = lbm::tiles_x(h->prm.nx), t = items[i].y;
+      titems[i] = {items[i].x, (t % ntx) * lbm::BX, (t / ntx) * tby,
+                   h->k.NP * 2 + (h->wall ? 1 : 0)};
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_titems, titems.data(),
+                          titems.size() * sizeof(lbm::TmaItem),
+                          cudaMemcpyHostToDevice, b->stream);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_list_off, off.data(), off.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
@@ -324,7 +642,9 @@ size_t lbm_nphase_batch_workspace_bytes(const lbm_nphase_params *params,
     items += tiles_for(p, 4);
   }
   total += align256b(ncases * sizeof(Case32));
+  total += align256b((size_t)ncases * 2 * sizeof(lbm::TmaMaps));
   total += align256b(items * sizeof(int2));
+  total += align256b(items * sizeof(lbm::TmaItem));
   total += align256b((size_t)(kMaxCtas + 1) * sizeof(int));
   total += align256b(items * sizeof(int));
   total += align256b(sizeof(int));
@@ -361,9 +681,13 @@ lbm_status lbm_nphase_batch_create(const lbm_nphase_params *params, int ncases,
   }
   b->d_cases = (Case32 *)(base + off);
   off += align256b(ncases * sizeof(Case32));
+  b->d_maps = (lbm::TmaMaps *)(base + off);
+  off += align256b((size_t)ncases * 2 * sizeof(lbm::TmaMaps));
   b->d_items = (int2 *)(base + off);
   b->items_cap = items;
   off += align256b(items * sizeof(int2));
+  b->d_titems = (lbm::TmaItem *)(base + off);
+  off += align256b(items * sizeof(lbm::TmaItem));
   b->d_list_off = (int *)(base + off);
   off += align256b((size_t)(kMaxCtas + 1) * sizeof(int));
   b->d_list = (int *)(base + off);
@@ -383,7 +707,34 @@ lbm_status lbm_nphase_batch_create(const lbm_nphase_params *params, int ncases,
       &per8, lbm::batch_kernel<LBM_FP32, 8>, lbm::BX * 8, 0);
   b->max_ctas[0] = std::min(std::max(per4, 1) * sms, kMaxCtas);
   b->max_ctas[1] = std::min(std::max(per8, 1) * sms, kMaxCtas);
-  lbm_nphase_batch_schedule s0 = {8, lbm::SCHED_DYNAMIC, 0};
+  // Pipelined kernel: every case must have tensor maps (FP32 maps of both
+  // buffers, copied next to the descriptors).
+  b->tma_ok = true;
+  for (lbm_nphase_t *h : b->cases) b->tma_ok = b->tma_ok && h->g.use_tma;
+  b->max_ctas_tma = 0;
+  if (b->tma_ok) {
+    std::vector<lbm::TmaMaps> maps(2 * (size_t)ncases);
+    for (int c = 0; c < ncases; ++c)
+      for (int q = 0; q < 2; ++q) maps[2 * c + q] = b->cases[c]->g.tma[q];
+    e = cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(lbm::TmaMaps),
+                        cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lbm::batch_kernel_tma,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)lbm::kBatchSmem);
+    int per = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per, lbm::batch_kernel_tma, lbm::BG::NTH, lbm::kBatchSmem);
+    if (e != cudaSuccess) {
+      b->cuda_err = (int)e;
+      lbm_nphase_batch_destroy(b);
+      return LBM_ECUDA;
+    }
+    b->max_ctas_tma = std::min(std::max(per, 1) * sms, kMaxCtas);
+  }
+  lbm_nphase_batch_schedule s0 = {8, lbm::SCHED_DYNAMIC, 0, 0, 1};
   st = build_schedule(b, s0);
   if (st != LBM_OK) {
     lbm_nphase_batch_destroy(b);
@@ -450,29 +801,37 @@ lbm_status lbm_nphase_batch_autotune(lbm_nphase_batch_t *b, int trial_steps,
   lbm_nphase_batch_schedule best = b->sched;
   float best_ms = 1e30f;
   lbm_status st = LBM_OK;
-  for (int ti = 0; ti < 2 && st == LBM_OK; ++ti)
-    for (int sc = 0; sc < 3 && st == LBM_OK; ++sc) {
-      lbm_nphase_batch_schedule s = {kTileHeights[ti], sc, 0};
-      st = build_schedule(b, s);
-      if (st != LBM_OK) break;
-      st = lbm_nphase_batch_step(b, 2);  // warm-up
-      if (st != LBM_OK) break;
-      cudaEventRecord(e0, b->stream);
-      st = lbm_nphase_batch_step(b, 2 * trial_steps);
-      cudaEventRecord(e1, b->stream);
-      if (st != LBM_OK) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        st = LBM_ECUDA;
-        break;
+  // Candidates: the generic kernel at tile heights 4 and 8 and the
+  // pipelined kernel (when every case has tensor maps), each with the
+  // strided, list and dynamic schedules (chunks of 1, 4 and 16 items).
+  std::vector<lbm_nphase_batch_schedule> cand;
+  for (int v = 0; v < (b->tma_ok ? 3 : 2); ++v)
+    for (int sc = 0; sc < 3; ++sc)
+      for (int ch : {1, 4, 16}) {
+        if (sc != lbm::SCHED_DYNAMIC && ch != 1) continue;
+        cand.push_back({kTileHeights[v < 2 ? v : 1], sc, 0, v == 2 ? 1 : 0, ch});
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= (float)(2 * trial_steps);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = b->sched;
-      }
+  for (size_t ci = 0; ci < cand.size() && st == LBM_OK; ++ci) {
+    st = build_schedule(b, cand[ci]);
+    if (st != LBM_OK) break;
+    st = lbm_nphase_batch_step(b, 2);  // warm-up
+    if (st != LBM_OK) break;
+    cudaEventRecord(e0, b->stream);
+    st = lbm_nphase_batch_step(b, 2 * trial_steps);
+    cudaEventRecord(e1, b->stream);
+    if (st != LBM_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = LBM_ECUDA;
+      break;
     }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)(2 * trial_steps);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = b->sched;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != LBM_OK) return st;

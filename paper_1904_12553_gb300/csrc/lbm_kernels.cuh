@@ -93,7 +93,7 @@ template <> __device__ __forceinline__ float to_S(float v) { return v; }
 template <typename S> __device__ __forceinline__ S to_S(double v) { return v; }
 
 // Kernel arguments: pointers of one step and the model constants in T.
-template <int P> struct KArgs {
+template <int P> struct alignas(16) KArgs {  // 16: bulk-copy granule
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
   int nx, ny;

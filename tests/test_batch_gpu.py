@@ -79,6 +79,70 @@ def test_batch_matches_single_grids(cases, singles, tby, sched):
     b.close()
 
 
+@pytest.mark.parametrize("sched", [0, 1, 2])
+def test_pipelined_batch_matches_single_grids(cases, singles, sched):
+    """TMA-pipelined tile body: items of different cases and N in flight in
+    the same CTA's stages."""
+    from paper_1904_12553_gb300 import Batch
+    b = Batch([w.params for w in cases])
+    b.set_schedule(8, sched, pipelined=True)
+    s = b.schedule()
+    assert s["pipelined"] == 1 and s["tile_height"] == 8
+    for i, w in enumerate(cases):
+        b.init(i, w.c0, w.u0)
+    b.step(6)
+    b.step(7)
+    for i in range(len(cases)):
+        _close(b.moments(i), singles[i])
+    b.close()
+
+
+@pytest.mark.parametrize("pipelined", [False, True])
+@pytest.mark.parametrize("chunk", [4, 16])
+def test_dynamic_chunks(cases, singles, pipelined, chunk):
+    """Dynamic schedule taking several consecutive items per atomic grab
+    (chunks that straddle cases and the end of the item list)."""
+    from paper_1904_12553_gb300 import Batch
+    b = Batch([w.params for w in cases])
+    b.set_schedule(8, 2, pipelined=pipelined, chunk=chunk)
+    assert b.schedule()["chunk"] == chunk
+    for i, w in enumerate(cases):
+        b.init(i, w.c0, w.u0)
+    b.step(13)
+    for i in range(len(cases)):
+        _close(b.moments(i), singles[i])
+    b.close()
+
+
+@pytest.mark.parametrize("ctas", [1, 3])
+def test_pipelined_batch_few_ctas(cases, singles, ctas):
+    """One or three persistent CTAs walk every item: many case switches per
+    CTA, both stages refilled across case boundaries."""
+    from paper_1904_12553_gb300 import Batch
+    b = Batch([w.params for w in cases])
+    b.set_schedule(8, 0, ctas=ctas, pipelined=True)
+    for i, w in enumerate(cases):
+        b.init(i, w.c0, w.u0)
+    b.step(13)
+    for i in range(len(cases)):
+        _close(b.moments(i), singles[i])
+    b.close()
+
+
+def test_pipelined_batch_needs_tensor_maps():
+    """A case whose nx is not a multiple of 8 has no tensor maps: the
+    pipelined schedule is refused and the generic one still runs."""
+    from paper_1904_12553_gb300 import Batch, LbmError
+    w = W.random_smooth(6, 3, 36, 20, precision="fp32", amp_u=0.02,
+                        sigma=W.sample_sigma(np.random.default_rng(6), 3,
+                                             accept=_accept))
+    b = Batch([w.params])
+    with pytest.raises(LbmError):
+        b.set_schedule(8, 0, pipelined=True)
+    assert b.schedule()["pipelined"] == 0
+    b.close()
+
+
 def test_autotune_and_reinit(cases, singles):
     from paper_1904_12553_gb300 import Batch
     b = Batch([w.params for w in cases])
@@ -88,6 +152,7 @@ def test_autotune_and_reinit(cases, singles):
     assert ms > 0
     s = b.schedule()
     assert s["tile_height"] in (4, 8) and s["schedule"] in (0, 1, 2)
+    assert s["pipelined"] in (0, 1)
     for i, w in enumerate(cases):     # the trials advanced the state
         b.init(i, w.c0, w.u0)
     b.step(13)
