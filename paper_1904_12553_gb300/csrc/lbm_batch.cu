@@ -379,7 +379,9 @@ __global__ void __launch_bounds__(BG::NTH, 1)
     if (d.c < 0) break;
     const bool ok = mbar_wait(bar + slot, (uint32_t)((j / S) & 1));
     const unsigned char *st = smem + slot * kStageStride;
-    const KArgs<LBM_FP32> &sa = *(const KArgs<LBM_FP32> *)(st + BSt::BYTES);
+    // The case's arguments by value: read from the stage once per tile
+    // (vector loads) and held in registers, not re-read at every use.
+    const KArgs<LBM_FP32> sa = *(const KArgs<LBM_FP32> *)(st + BSt::BYTES);
     float *sphi = (float *)(smem + S * kStageStride + (j & 1) * BSt::SPHI);
     const int x0 = d.x0, y0 = d.y0;
     TileRegs r;
@@ -531,8 +533,15 @@ lbm_status build_schedule(lbm_nphase_batch_t *b, lbm_nphase_batch_schedule s) {
     const lbm_nphase_params &p = b->cases[c]->prm;
     return (double)tiles_for(p, tby) * p.N;
   };
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return cost(x) > cost(y); });
+  // Cases of one (N - 1, walls) class are kept together, so that the CTAs
+  // running at one time mostly execute the same code.
+  auto klass = [&](int c) {
+    return b->cases[c]->k.NP * 2 + (b->cases[c]->wall ? 1 : 0);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (klass(x) != klass(y)) return klass(x) > klass(y);
+    return cost(x) > cost(y);
+  });
   std::vector<int2> items;
   std::vector<double> icost;
   for (int c : order) {

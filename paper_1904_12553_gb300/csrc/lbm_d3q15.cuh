@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
       ph[i] = sphi[i * PL + (lz * H + ly) * W + lx];
       stencil3<T, W, H>(sphi + i * PL, lz, ly, lx, gp[i], lp[i]);
     }
-    local_algebra<P, NP>(a, ph, cc, rho, hf);
+    local_algebra<P, NP, !NU>(a, ph, cc, rho, hf);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       if constexpr (NU) {

@@ -225,14 +225,36 @@ __device__ __forceinline__ int wrap_y(int v, int n) {
 }
 
 // Volume fractions (Eq. N18), density (Eq. N29) and h_i of Eq. N17 at one
-// node from its order parameters.
-template <int P, int NP>
+// node from its order parameters. With equal pure-phase densities (EQ) the
+// maps reduce exactly to c_k = phi_k + (1 - S)/N (k < N - 1),
+// c_{N-1} = (1 - S)/N with S = sum_j phi_j, rho = rho~ and
+// h_i = f_i - (1/N) sum_k f_k, f_k = c_k (1 - c_k)(1 - 2 c_k).
+template <int P, int NP, bool EQ = false>
 __device__ __forceinline__ void local_algebra(const KArgs<P> &a,
                                               const typename Prec<P>::T *ph,
                                               typename Prec<P>::T *c,
                                               typename Prec<P>::T &rho,
                                               typename Prec<P>::T *hf) {
   typedef typename Prec<P>::T T;
+  if constexpr (EQ) {
+    constexpr T invN = T(1) / T(NP + 1);
+    T S = T(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) S += ph[j];
+    const T base = (T(1) - S) * invN;
+    T f[NP + 1], F = T(0);
+#pragma unroll
+    for (int k = 0; k <= NP; ++k) {
+      const T ck = k < NP ? ph[k] + base : base;
+      c[k] = ck;
+      f[k] = ck * (T(1) - ck) * (T(1) - T(2) * ck);
+      F += f[k];
+    }
+    rho = a.rho_base;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) hf[i] = f[i] - F * invN;
+    return;
+  }
   T vp[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) vp[j] = a.off[j] + a.mul[j] * ph[j];
@@ -356,7 +378,7 @@ __device__ __forceinline__ void node_macros(const KArgs<P> &a,
       if constexpr (G40)
         gradient_mixed<T, SW>(sphi + i * plane, ly, lx, m.gpx[i], m.gpy[i]);
     }
-    local_algebra<P, NP>(a, m.ph, m.cc, m.rho, hf);
+    local_algebra<P, NP, !NU>(a, m.ph, m.cc, m.rho, hf);
     if constexpr (NU) {
 #pragma unroll
       for (int i = 0; i < NP; ++i) m.Cv[i] = sC[i * cplane + cly * CW + clx];
