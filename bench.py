@@ -180,9 +180,11 @@ def make_workload(prec="fp32", n=2048, accept=None):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def time_form(w, prec, steps, warmup, dist=None):
+def time_form(w, prec, steps, warmup, dist=None, segments=None):
     """Device time of `steps` back-to-back time steps (CUDA events on the
-    solver's stream), max over ranks."""
+    solver's stream), max over ranks. If `segments` is a list, the steps are
+    also split into five equal runs bracketed by events and their times (ms)
+    are appended to it."""
     import torch
     from paper_1904_12553_gb300 import Solver
 
@@ -194,16 +196,21 @@ def time_form(w, prec, steps, warmup, dist=None):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    nseg = 5 if segments is not None and steps >= 5 else 1
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nseg + 1)]
+    bounds = [steps * i // nseg for i in range(nseg + 1)]
     wall0 = time.time()
-    e0.record(s.stream)
-    for _ in range(steps):
-        s.step(1)
-    e1.record(s.stream)
+    ev[0].record(s.stream)
+    for i in range(nseg):
+        for _ in range(bounds[i + 1] - bounds[i]):
+            s.step(1)
+        ev[i + 1].record(s.stream)
     torch.cuda.synchronize()
     wall1 = time.time()
-    ms = e0.elapsed_time(e1)
+    ms = ev[0].elapsed_time(ev[-1])
+    if segments is not None and nseg > 1:
+        segments.extend((ev[i].elapsed_time(ev[i + 1]), bounds[i + 1] - bounds[i])
+                        for i in range(nseg))
     if dist:
         dist.barrier()
         ms = max_over_ranks(ms, dist, "cuda")
@@ -336,8 +343,17 @@ def batch_run(steps=50, ncases=256):
 
 def cpu_baseline(steps=3):
     """The FP64 oracle on the full workload, timed on this host's cores in a
-    fresh process (OpenMP over rows, all cores)."""
+    fresh process (OpenMP over rows): all cores over `steps` steps, and one
+    thread over one step."""
     cores = os.cpu_count() or 1
+    out = _oracle_run(steps, cores)
+    one = _oracle_run(1, 1)
+    if one.get("value") is not None:
+        out["single_thread"] = one
+    return out
+
+
+def _oracle_run(steps, cores):
     code = (
         "import sys, time, json\n"
         f"sys.path.insert(0, {ROOT!r}); sys.path.insert(0, {os.path.join(ROOT, 'oracle')!r})\n"
@@ -367,6 +383,16 @@ def cpu_baseline(steps=3):
                       f"({d['seconds']:.1f} s)"}
 
 
+def segment_summary(segs, V):
+    """Best and median rate over the timed region's five equal runs."""
+    if not segs:
+        return None
+    rates = [V * n / (t / 1e3) / 1e6 for t, n in segs]
+    return {"n": len(rates), "mlups_best": max(rates),
+            "mlups_median": statistics.median(rates),
+            "mlups_worst": min(rates)}
+
+
 def run_ours(args, dist, rank, world):
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -379,8 +405,9 @@ def run_ours(args, dist, rank, world):
     w = make_workload("fp32", n=args.n, accept=accept_sigma(5))
     N, V = w.params["N"], w.V
     sampler = ClockSampler(local) if rank == 0 else None
+    segs = []
     ms, (wa, wb), mass, ke, kernel = time_form(w, "fp32", args.steps,
-                                               args.warmup, dist)
+                                               args.warmup, dist, segs)
     if sampler:
         sampler.mark(wa, wb)
     clocks = sampler.stop() if sampler else None
@@ -444,6 +471,7 @@ def run_ours(args, dist, rank, world):
         "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
+        "segments": segment_summary(segs, V),
         "clocks": clocks,
         "forms": forms,
         "check": {"mass": list(map(float, mass)), "ke": float(ke)},
