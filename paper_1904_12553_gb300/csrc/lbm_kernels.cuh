@@ -762,6 +762,13 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 //  - Tile height 8: FP32 with 32 x 12 tiles (384 threads, 225 KB) ran 30%
 //    slower; a stage without halo columns (wrapped ring columns from global
 //    memory, two CTAs per SM) ran 48% slower.
+//  - Also measured and rejected (FP32 / 16-bit): g and u(t-1) loaded from
+//    global memory before the wait instead of staged, -19% (and a third
+//    stage on top of that, a further -6%); releasing the stage right after
+//    the phi barrier (u(t-1) read into registers, one barrier per tile),
+//    -9% / -24%; ring phi split over (position, phase) pairs on all warps,
+//    -1.5% / -35%. Instrumented, the FP32 kernel spends 13-19% of its time
+//    in the stage wait.
 template <int P> struct TmaGeom {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
