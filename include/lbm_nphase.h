@@ -62,8 +62,11 @@ typedef enum {
 /* Model parameters, as the paper states them (Sections 2-4). */
 typedef struct {
   int32_t N;           /* number of phases, 2..5 */
-  int32_t nx, ny;      /* grid size, >= 1 each */
-  int32_t nz;          /* third dimension of a D3Q15 grid (>= 1); D2Q9: 0 or 1 */
+  int32_t nx, ny;      /* grid size, >= 1 each; nx <= 2^20; D2Q9:
+                          ny <= 524280, D3Q15: ny <= 262140 (the generic
+                          kernels' launch grid); nx*ny*nz <= 2^34 */
+  int32_t nz;          /* third dimension of a D3Q15 grid (1..131070); D2Q9:
+                          0 or 1 */
   int32_t lattice;     /* 0: D2Q9 (two dimensions); 1: D3Q15 (three; Section
                           3.1), central scheme only */
   int32_t wall_y;      /* 0: periodic in y; 1: halfway bounce-back walls at

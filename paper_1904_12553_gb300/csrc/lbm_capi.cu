@@ -131,6 +131,13 @@ lbm_status validate(const lbm_nphase_params *p) {
   if (p->lattice == 0 && p->nz != 0 && p->nz != 1) return LBM_EINVAL;
   if (p->lattice == 1 && (p->nz < 1 || p->nz > (1 << 20) || p->grad_scheme != 0))
     return LBM_EINVAL;
+  // The generic kernels launch one CTA per tile on a 2-D (D2Q9: 32 x 8
+  // tiles) or 3-D (D3Q15: 32 x 4 x 2 tiles) grid, at most 65535 tiles along
+  // y and z.
+  if (p->lattice == 0 && lbm::tiles_y(p->ny) > 65535) return LBM_EINVAL;
+  if (p->lattice == 1 &&
+      (lbm::tiles3_y(p->ny) > 65535 || lbm::tiles3_z(p->nz) > 65535))
+    return LBM_EINVAL;
   if ((double)p->nx * (double)p->ny * (double)(p->nz > 1 ? p->nz : 1) >
       17179869184.0)
     return LBM_EINVAL;

@@ -120,6 +120,29 @@ def test_invalid_lattice_parameters_rejected(lib, bad):
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("shape,ok", [
+    (dict(nx=8, ny=524280), True), (dict(nx=8, ny=524281), False),
+    (dict(nx=1 << 20, ny=4), True), (dict(nx=(1 << 20) + 1, ny=4), False),
+    (dict(lattice=1, nx=8, ny=262140, nz=2), True),
+    (dict(lattice=1, nx=8, ny=262141, nz=2), False),
+    (dict(lattice=1, nx=8, ny=8, nz=131070), True),
+    (dict(lattice=1, nx=8, ny=8, nz=131071), False),
+])
+def test_grid_extent_limits(lib, shape, ok):
+    """The largest extents the launch grids allow are accepted, one more
+    node is rejected."""
+    base = W.random_smooth3(0, 3, 8, 8, 8) if shape.get("lattice") else \
+        W.static_drops()
+    p = {**base.params, **shape}
+    if ok:
+        P.lbm_nphase_derive(p)
+        assert P.lbm_nphase_workspace_bytes(p) > 0
+    else:
+        with pytest.raises(P.LbmError) as e:
+            P.lbm_nphase_derive(p)
+        assert e.value.status == 1
+
+
 def test_d3q15_workspace(lib):
     p3 = W.base_params3(3, 16, 12, 10, 1e-3, precision="fp32")
     b = P.lbm_nphase_workspace_bytes(p3)

@@ -295,6 +295,34 @@ def test_quiescent_exact(prec, wall):
     assert np.ptp(g["phi"], axis=(1, 2)).max() == 0.0
 
 
+@pytest.mark.parametrize("pure", [0, 3])
+def test_pure_phase_stationary(pure):
+    """Degenerate mixture: one phase fills the domain (c_k = 1; for the last
+    phase every phi_i = -1). Nothing may move."""
+    frac = [0.0] * 4
+    frac[pure] = 1.0
+    w = W.quiescent(4, 40, 19, frac=frac, rho=[2, 1, 3, 7], precision="fp64")
+    g = gpu_run(w, 200)
+    assert np.abs(g["u"]).max() == 0.0
+    assert np.ptp(g["phi"], axis=(1, 2)).max() == 0.0
+    np.testing.assert_allclose(g["c"][pure], 1.0, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 524280), (1 << 20, 4)])
+def test_maximum_extents_fp32(nx, ny):
+    """The largest extents the launch grids allow: one tile wide with 65535
+    tile rows, and 32768 tile columns of a four-row grid. Two steps against
+    the oracle."""
+    rng = np.random.default_rng(nx + ny)
+    w = W.random_smooth(5, 2, nx, ny, precision="fp32", amp_u=0.02,
+                        sigma=W.sample_sigma(rng, 2))
+    g = gpu_run(w, 2)
+    o = oracle_run(w, 2)
+    assert maxdiff(g["phi"], o["phi"]) <= 2e-6
+    assert maxdiff(g["u"], o["u"]) <= 1e-4 * np.abs(o["u"]).max()
+    np.testing.assert_allclose(g["c"].sum(0), 1.0, atol=1e-6)
+
+
 def test_deterministic():
     w = W.random_smooth(11, 4, 67, 33, rho=[1, 2, 3, 4], amp_u=0.01)
     a = gpu_run(w, 50)
