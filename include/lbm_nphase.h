@@ -264,11 +264,12 @@ lbm_status lbm_nphase_set_state(lbm_nphase_t *h, const void *src, size_t bytes);
 /* Number of time steps taken since the last init. */
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
 
-/* 1 if lbm_nphase_step runs the TMA-pipelined kernel for this handle (FP32
- * and 16-bit forms, equal pure-phase densities, nx a multiple of 8), 0 if it
- * runs the generic tile kernel. Setting the environment variable
+/* Which kernel lbm_nphase_step runs for this handle: 1 the TMA-pipelined
+ * D2Q9 kernel (FP32 and 16-bit forms, equal pure-phase densities, nx a
+ * multiple of 8), 2 the z-marching D3Q15 kernel (equal densities, every
+ * storage form), 0 the generic tile kernel. Setting the environment variable
  * LBM_NPHASE_KERNEL=generic before lbm_nphase_create selects the generic
- * kernel everywhere. Both compute the same step. */
+ * kernels everywhere. All compute the same step. */
 int lbm_nphase_uses_pipelined_kernel(const lbm_nphase_t *h);
 
 /* The last CUDA error code seen by the handle (0 if none). */

@@ -262,8 +262,8 @@ def lbm_nphase_set_state(handle: int, src_ptr: int, nbytes: int):
            "lbm_nphase_set_state")
 
 
-def lbm_nphase_uses_pipelined_kernel(handle: int) -> bool:
-    return bool(load_library().lbm_nphase_uses_pipelined_kernel(
+def lbm_nphase_uses_pipelined_kernel(handle: int) -> int:
+    return int(load_library().lbm_nphase_uses_pipelined_kernel(
         C.c_void_p(handle)))
 
 
@@ -366,7 +366,13 @@ class Solver:
 
     @property
     def pipelined(self) -> bool:
-        return lbm_nphase_uses_pipelined_kernel(self.handle)
+        """True if steps run the TMA-pipelined D2Q9 kernel."""
+        return lbm_nphase_uses_pipelined_kernel(self.handle) == 1
+
+    @property
+    def step_kernel(self) -> str:
+        return {1: "pipelined (TMA)", 2: "z-marching 3-D"}.get(
+            lbm_nphase_uses_pipelined_kernel(self.handle), "generic tile")
 
     @property
     def steps_taken(self) -> int:

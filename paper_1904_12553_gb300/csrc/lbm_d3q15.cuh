@@ -112,8 +112,192 @@ __device__ __forceinline__ size_t node3(int x, int y, int z, int nx, int ny,
   return ((size_t)wrap(z, nz) * ny + wrap_y<WALL>(y, ny)) * nx + wrap(x, nx);
 }
 
+// The values a D3Q15 step reads at its own node: h^i_0 (FP64) or d^i_0 and
+// h^i_1..14 (converted to T, stored units for the 16-bit forms), g_1..14 (the
+// same), phi_i(t-1) and u(t-1).
+template <int P, int NP> struct Own3 {
+  typedef typename Prec<P>::T T;
+  T h[NP][15], g[15], pp[NP], up[3];
+};
+
+template <int P, int NP>
+__device__ __forceinline__ void load_own3(const KArgs<P> &a, size_t q,
+                                          Own3<P, NP> &o) {
+  const size_t V = a.V;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    o.h[i][0] = ldg(a.h0_in + (size_t)i * V + q);
+#pragma unroll
+    for (int k = 1; k < 15; ++k) o.h[i][k] = load_hm3<P>(a, i, k, q);
+    o.pp[i] = ldg(a.pp_in + (size_t)i * V + q);
+  }
+#pragma unroll
+  for (int k = 1; k < 15; ++k) o.g[k] = to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) o.up[d] = a.u_prev[(size_t)d * V + q];
+}
+
+// phi_i from a node's values in registers, summed in the order of node_phi3.
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T node_phi3r(
+    const typename Prec<P>::T *h, typename Prec<P>::T pp,
+    typename Prec<P>::T &err, typename Prec<P>::T sh_ld) {
+  typedef typename Prec<P>::T T;
+  T small = h[0];
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    if constexpr (Prec<P>::MIX)
+      small = __fmaf_rn(w3_of<T>(k) * sh_ld, h[k], small);
+    else
+      small = __fadd_rn_T(small, h[k]);
+  }
+  if constexpr (P == LBM_FP64) {
+    err = T(0);
+    return small;
+  } else {
+    const T s = __fadd_rn(pp, small);
+    const T bb = __fsub_rn(s, pp);
+    err = __fadd_rn(__fsub_rn(pp, __fsub_rn(s, bb)), __fsub_rn(small, bb));
+    return s;
+  }
+}
+
+// F = sum_i C_i grad phi_i + rho g, u (Eq. N22_1) and p (Eq. N23 on D3Q15)
+// of one node from its stencil results and its NS populations g[1..14]
+// (stored units).
+template <int P, int NP>
+__device__ __forceinline__ void macros3(
+    const KArgs<P> &a, const typename Prec<P>::T (&gp)[NP][3],
+    const typename Prec<P>::T *Cv, typename Prec<P>::T rho,
+    const typename Prec<P>::T *gr, const typename Prec<P>::T (&g)[15],
+    typename Prec<P>::T (&u)[3], typename Prec<P>::T (&F)[3],
+    typename Prec<P>::T &uu, typename Prec<P>::T &pr) {
+  typedef typename Prec<P>::T T;
+  const T grav[3] = {a.grav[0], a.grav[1], a.grav_z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d] = rho * grav[d];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) F[d] += Cv[i] * gp[i][d];
+  }
+  T mo[3] = {T(0), T(0), T(0)}, sg = T(0);
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    T gk = g[k];
+    if constexpr (Prec<P>::MIX) gk *= w3_of<T>(k) * a.sg_ld;
+    mo[0] += T(c3x(k)) * gk;
+    mo[1] += T(c3y(k)) * gk;
+    mo[2] += T(c3z(k)) * gk;
+    sg += gk;
+  }
+  const T rinv = T(1) / rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = (mo[d] + T(0.5) * F[d]) * rinv;
+  uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
+  // Eq. N23 on D3Q15: c_s^2 / (1 - w_0) = 3/7, s_0 = -w_0 |u|^2 / (2 c_s^2)
+  pr = T(3.0 / 7.0) * (sg + T(0.5) * ugr - rho * T(2.0 / 9.0) * T(1.5) * uu);
+}
+
+// Collisions of one D3Q15 node (Eqs. 24, N24 with Eqs. 25, N20_1, N25-N27),
+// folded as in the D2Q9 kernels, and push streaming; phi(t) and u(t) become
+// the next step's phi(t-1) and u(t-1).
 template <int P, int NP, bool NU, bool WALL>
-__global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
+__device__ __forceinline__ void collide3(
+    const KArgs<P> &a, int nz, const typename Prec<P>::T *ph,
+    const typename Prec<P>::T *Cv, typename Prec<P>::T rho,
+    const typename Prec<P>::T *gr, const typename Prec<P>::T *J,
+    const Own3<P, NP> &o, const typename Prec<P>::T (&u)[3],
+    const typename Prec<P>::T (&F)[3], typename Prec<P>::T uu,
+    typename Prec<P>::T pr, size_t q, int gx, int gy, int gz) {
+  typedef typename Prec<P>::T T;
+  const int nx = a.nx, ny = a.ny;
+  const size_t V = a.V;
+  size_t dst[15];
+  int dk[15];
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    const int yy = gy + c3y(k);
+    if (WALL && (yy < 0 || yy >= ny)) {
+      dst[k] = q;
+      dk[k] = opp3(k);
+    } else {
+      dst[k] = node3<WALL>(gx + c3x(k), yy, gz + c3z(k), nx, ny, nz);
+      dk[k] = k;
+    }
+  }
+  constexpr bool MIX = Prec<P>::MIX;
+  const T tg = a.tg_inv, ff = a.ffac;
+  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const T Ju = (J[0] * u[0] + J[1] * u[1] + J[2] * u[2]) * a.jfac;
+  const T A0 = tg * (T(3) * pr - T(1.5) * rho * uu) - ff * (T(3) * uF + T(1.5) * Ju);
+  const T B1 = T(3) * tg * rho, B2 = T(4.5) * tg * rho;
+  const T C1 = T(3) * ff, D1 = T(9) * ff, E1 = T(3) * ff, E2 = T(4.5) * ff * a.jfac;
+  const T keep_g = T(1) - tg;
+#pragma unroll
+  for (int k = 1; k < 15; ++k) {
+    const T cx = T(c3x(k)), cy = T(c3y(k)), cz = T(c3z(k));
+    const T cu = cx * u[0] + cy * u[1] + cz * u[2];
+    const T cF = cx * F[0] + cy * F[1] + cz * F[2];
+    T inner = B1 + B2 * cu + D1 * cF;
+    if constexpr (NU)
+      inner += E1 * (cx * gr[0] + cy * gr[1] + cz * gr[2]) +
+               E2 * (cx * J[0] + cy * J[1] + cz * J[2]);
+    const T t = A0 + C1 * cF + cu * inner;
+    if constexpr (MIX)
+      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] =
+          to_S<typename Prec<P>::Sm>(keep_g * o.g[k] + a.sg_st * t);
+    else
+      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = keep_g * o.g[k] + w3_of<T>(k) * t;
+  }
+  const T *up = o.up;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const T pp = o.pp[i];
+    const T ti = a.tau_inv[i], aC = a.a[i] * Cv[i];
+    T al = ti * aC, b[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      b[d] = T(3) * (ti * ph[i] * u[d] + a.src[i] * (ph[i] * u[d] - pp * up[d]));
+    if constexpr (MIX) {
+      al *= a.sh_st;
+      for (int d = 0; d < 3; ++d) b[d] *= a.sh_st;
+    }
+    const T keep = T(1) - ti;
+    T moving_sum = T(0), perr;
+    // phi's rounding error of this node, from its values as loaded
+    node_phi3r<P>(o.h[i], pp, perr, a.sh_ld);
+#pragma unroll
+    for (int k = 1; k < 15; ++k) {
+      const T t = al + T(c3x(k)) * b[0] + T(c3y(k)) * b[1] + T(c3z(k)) * b[2];
+      const T hk = o.h[i][k];
+      const size_t oo = ((size_t)(i * 14 + dk[k] - 1)) * V + dst[k];
+      if constexpr (MIX) {
+        const auto sv = to_S<typename Prec<P>::Sm>(keep * hk + t);
+        a.hm_out[oo] = sv;
+        moving_sum = __fmaf_rn(w3_of<T>(k) * a.sh_ld, to_T(sv), moving_sum);
+      } else {
+        const T hs = keep * hk + w3_of<T>(k) * t;
+        a.hm_out[oo] = hs;
+        moving_sum = __fadd_rn_T(moving_sum, hs);
+      }
+    }
+    T rest;
+    if constexpr (P == LBM_FP64) {
+      rest = keep * o.h[i][0] + ti * (ph[i] + (w3_of<T>(0) - T(1)) * aC);
+    } else {
+      rest = __fsub_rn(perr, moving_sum);
+    }
+    a.h0_out[(size_t)i * V + q] = rest;
+    a.pp_out[(size_t)i * V + q] = ph[i];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) a.u_prev[(size_t)d * V + q] = u[d];
+}
+
+template <int P, int NP, bool NU, bool WALL>
+__global__ void __launch_bounds__(NT3, P == LBM_FP64 ? 1 : 2)
+    tile3_kernel(const KArgs3<P> A) {
   typedef typename Prec<P>::T T;
   const KArgs<P> &a = A.a;
   constexpr int RC = NU ? 1 : 0;       // C ring radius
@@ -133,6 +317,7 @@ __global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
   const int x0 = blockIdx.x * BX3, y0 = blockIdx.y * BY3, z0 = blockIdx.z * BZ3;
   const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
   const bool active = gx < nx && gy < ny && gz < nz;
+  const size_t q = active ? (((size_t)gz * ny + gy) * nx + gx) : 0;
 
   // 1. phi on the box (tile + halo R), wrapped / ghost coordinates.
   for (int r = tid; r < PL; r += NT3) {
@@ -182,7 +367,6 @@ __global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
   }
 
   // 3. Own node: stencils, C, F, u, p.
-  const size_t q = active ? (((size_t)gz * ny + gy) * nx + gx) : 0;
   const int lz = tz + R, ly = ty + R, lx = tx + R;
   T ph[NP], gp[NP][3], Cv[NP], cc[NP + 1], rho;
   {
@@ -218,34 +402,11 @@ __global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
       }
     }
   }
-  T F[3];
-  const T grav[3] = {a.grav[0], a.grav[1], A.a.grav_z};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    F[d] = rho * grav[d];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) F[d] += Cv[i] * gp[i][d];
-  }
-  T g[15], mo[3] = {T(0), T(0), T(0)}, sg = T(0);
-#pragma unroll
-  for (int k = 1; k < 15; ++k) {
-    g[k] = active ? to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q)) : T(0);
-    T gk = g[k];
-    if constexpr (Prec<P>::MIX) gk *= w3_of<T>(k) * a.sg_ld;
-    mo[0] += T(c3x(k)) * gk;
-    mo[1] += T(c3y(k)) * gk;
-    mo[2] += T(c3z(k)) * gk;
-    sg += gk;
-  }
-  const T rinv = T(1) / rho;
-  T u[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) u[d] = (mo[d] + T(0.5) * F[d]) * rinv;
-  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const T ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
-  // Eq. N23 on D3Q15: c_s^2 / (1 - w_0) = 3/7, s_0 = -w_0 |u|^2 / (2 c_s^2)
-  const T pr = T(3.0 / 7.0) * (sg + T(0.5) * ugr - rho * T(2.0 / 9.0) * T(1.5) * uu);
-
+  // own-node values (node 0 stands in for inactive threads)
+  Own3<P, NP> own;
+  load_own3<P, NP>(a, q, own);
+  T F[3], u[3], uu, pr;
+  macros3<P, NP>(a, gp, Cv, rho, gr, own.g, u, F, uu, pr);
   if (a.mode == MODE_MOMENTS) {
     if (!active) return;
     if (a.o_phi)
@@ -281,89 +442,130 @@ __global__ void __launch_bounds__(NT3) tile3_kernel(const KArgs3<P> A) {
   }
   if (!active) return;
 
-  // 4. Collisions (Eqs. 24, N24 with Eqs. 25, N20_1, N25-N27), folded as in
-  //    the D2Q9 kernels, and push streaming.
-  size_t dst[15];
-  int dk[15];
+  collide3<P, NP, NU, WALL>(a, nz, ph, Cv, rho, gr, J, own, u, F, uu, pr, q,
+                            gx, gy, gz);
+}
+
+// ---------------------------------------------------------------------------
+// z-marching step kernel (equal densities, central scheme). A CTA owns a
+// 32 x 8 column of the grid and walks a slab of z planes. phi of plane z + 1
+// is summed on the column's tile and its xy ring into a rolling window of
+// three planes (z - 1, z, z + 1) in shared memory, so a node's phi is summed
+// once per slab (plus the 84 ring positions per 256 nodes of a plane)
+// instead of on a 3-D halo box around every tile; the 14 stencil neighbours
+// of a node of plane z then come from the window. The per-node step is the
+// one of tile3_kernel (macros3, collide3).
+// ---------------------------------------------------------------------------
+constexpr int MX3 = 32, MY3 = 8, MT3 = MX3 * MY3;
+
+// Eq. N31 on D3Q15 from three planes (z - 1, z, z + 1) of stride W, pairs of
+// opposite velocities summed in the order of stencil3.
+template <typename T, int W>
+__device__ __forceinline__ void stencil3w(const T *pm, const T *p0, const T *pp,
+                                          int ly, int lx, T *g, T &lap) {
+  const int o = ly * W + lx;
+  const T c = p0[o];
+  T gx = T(0), gy = T(0), gz = T(0), l = T(0);
 #pragma unroll
   for (int k = 1; k < 15; ++k) {
-    const int yy = gy + c3y(k);
-    if (WALL && (yy < 0 || yy >= ny)) {
-      dst[k] = q;
-      dk[k] = opp3(k);
-    } else {
-      dst[k] = node3<WALL>(gx + c3x(k), yy, gz + c3z(k), nx, ny, nz);
-      dk[k] = k;
-    }
+    if (opp3(k) < k) continue;
+    const T *plus = c3z(k) > 0 ? pp : (c3z(k) < 0 ? pm : p0);
+    const T *minus = c3z(k) > 0 ? pm : (c3z(k) < 0 ? pp : p0);
+    const int d = c3y(k) * W + c3x(k);
+    const T p = plus[o + d], m = minus[o - d];
+    const T wd = w3_of<T>(k) * (p - m);
+    gx += T(c3x(k)) * wd;
+    gy += T(c3y(k)) * wd;
+    gz += T(c3z(k)) * wd;
+    l += w3_of<T>(k) * (p + m - T(2) * c);
   }
-  constexpr bool MIX = Prec<P>::MIX;
-  const T tg = a.tg_inv, ff = a.ffac;
-  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-  const T Ju = (J[0] * u[0] + J[1] * u[1] + J[2] * u[2]) * a.jfac;
-  const T A0 = tg * (T(3) * pr - T(1.5) * rho * uu) - ff * (T(3) * uF + T(1.5) * Ju);
-  const T B1 = T(3) * tg * rho, B2 = T(4.5) * tg * rho;
-  const T C1 = T(3) * ff, D1 = T(9) * ff, E1 = T(3) * ff, E2 = T(4.5) * ff * a.jfac;
-  const T keep_g = T(1) - tg;
+  g[0] = T(3) * gx;
+  g[1] = T(3) * gy;
+  g[2] = T(3) * gz;
+  lap = T(6) * l;
+}
+
+template <int P, int NP, bool WALL>
+__global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
+    march3_kernel(const KArgs3<P> A, int zlen) {
+  typedef typename Prec<P>::T T;
+  const KArgs<P> &a = A.a;
+  constexpr int SW = MX3 + 2, SH = MY3 + 2, PL = SW * SH;
+  __shared__ T win[3][NP][PL];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MX3 + tx;
+  const int nx = a.nx, ny = a.ny, nz = A.nz;
+  const int x0 = blockIdx.x * MX3, y0 = blockIdx.y * MY3;
+  const int zs = blockIdx.z * zlen;
+  const int ze = zs + zlen < nz ? zs + zlen : nz;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool col = gx < nx && gy < ny;
+  // window slot of plane z (z >= zs - 1)
+  auto slot = [&](int z) { return (z - zs + 1) % 3; };
+  // phi of plane z on the tile (wrapped where the tile overhangs the grid)
+  // and its xy ring
+  auto plane_phi = [&](int z) {
+    T(*w)[PL] = win[slot(z)];
+    const int zz = wrap(z, nz);
+    {
+      const size_t q = ((size_t)zz * ny + wrap_y<WALL>(gy, ny)) * nx + wrap(gx, nx);
 #pragma unroll
-  for (int k = 1; k < 15; ++k) {
-    const T cx = T(c3x(k)), cy = T(c3y(k)), cz = T(c3z(k));
-    const T cu = cx * u[0] + cy * u[1] + cz * u[2];
-    const T cF = cx * F[0] + cy * F[1] + cz * F[2];
-    T inner = B1 + B2 * cu + D1 * cF;
-    if constexpr (NU)
-      inner += E1 * (cx * gr[0] + cy * gr[1] + cz * gr[2]) +
-               E2 * (cx * J[0] + cy * J[1] + cz * J[2]);
-    const T t = A0 + C1 * cF + cu * inner;
-    if constexpr (MIX)
-      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] =
-          to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
-    else
-      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = keep_g * g[k] + w3_of<T>(k) * t;
-  }
-  const T up[3] = {a.u_prev[q], a.u_prev[V + q], a.u_prev[2 * V + q]};
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    const T pp = ldg(a.pp_in + (size_t)i * V + q);
-    const T ti = a.tau_inv[i], aC = a.a[i] * Cv[i];
-    T al = ti * aC, b[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      b[d] = T(3) * (ti * ph[i] * u[d] + a.src[i] * (ph[i] * u[d] - pp * up[d]));
-    if constexpr (MIX) {
-      al *= a.sh_st;
-      for (int d = 0; d < 3; ++d) b[d] *= a.sh_st;
-    }
-    const T keep = T(1) - ti;
-    T moving_sum = T(0), perr;
-    // recompute phi's rounding error of this node (stored values unchanged)
-    node_phi3<P>(a, i, q, perr);
-#pragma unroll
-    for (int k = 1; k < 15; ++k) {
-      const T t = al + T(c3x(k)) * b[0] + T(c3y(k)) * b[1] + T(c3z(k)) * b[2];
-      const T hk = load_hm3<P>(a, i, k, q);
-      const size_t o = ((size_t)(i * 14 + dk[k] - 1)) * V + dst[k];
-      if constexpr (MIX) {
-        const auto sv = to_S<typename Prec<P>::Sm>(keep * hk + t);
-        a.hm_out[o] = sv;
-        moving_sum = __fmaf_rn(w3_of<T>(k) * a.sh_ld, to_T(sv), moving_sum);
-      } else {
-        const T hs = keep * hk + w3_of<T>(k) * t;
-        a.hm_out[o] = hs;
-        moving_sum = __fadd_rn_T(moving_sum, hs);
+      for (int i = 0; i < NP; ++i) {
+        T e;
+        w[i][(ty + 1) * SW + tx + 1] = node_phi3<P>(a, i, q, e);
       }
     }
-    T rest;
-    if constexpr (P == LBM_FP64) {
-      const T h0 = ldg(a.h0_in + (size_t)i * V + q);
-      rest = keep * h0 + ti * (ph[i] + (w3_of<T>(0) - T(1)) * aC);
-    } else {
-      rest = __fsub_rn(perr, moving_sum);
-    }
-    a.h0_out[(size_t)i * V + q] = rest;
-    a.pp_out[(size_t)i * V + q] = ph[i];
-  }
+    constexpr int NRING = PL - MT3;
+    static_assert(NRING <= MT3, "one ring position per thread");
+    if (tid < NRING) {
+      int lx, ly;
+      ring_pos_1<MY3>(tid, lx, ly);
+      const size_t q = node3<WALL>(x0 - 1 + lx, y0 - 1 + ly, zz, nx, ny, nz);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) a.u_prev[(size_t)d * V + q] = u[d];
+      for (int i = 0; i < NP; ++i) {
+        T e;
+        w[i][ly * SW + lx] = node_phi3<P>(a, i, q, e);
+      }
+    }
+  };
+  plane_phi(zs - 1);
+  plane_phi(zs);
+  for (int z = zs; z < ze; ++z) {
+    // this plane's own-node loads first, in flight while phi of the next
+    // plane is summed
+    const size_t q = col ? ((size_t)z * ny + gy) * nx + gx : 0;
+    Own3<P, NP> own;
+    load_own3<P, NP>(a, q, own);
+    plane_phi(z + 1);
+    __syncthreads();
+    if (col) {
+      const T(*wm)[PL] = win[slot(z - 1)];
+      const T(*w0)[PL] = win[slot(z)];
+      const T(*wp)[PL] = win[slot(z + 1)];
+      T ph[NP], gp[NP][3], Cv[NP], cc[NP + 1], rho;
+      {
+        T lp[NP], hf[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          ph[i] = w0[i][(ty + 1) * SW + tx + 1];
+          stencil3w<T, SW>(wm[i], w0[i], wp[i], ty + 1, tx + 1, gp[i], lp[i]);
+        }
+        local_algebra<P, NP, true>(a, ph, cc, rho, hf);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          T Ci = a.bulk * hf[i];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+          Cv[i] = Ci;
+        }
+      }
+      const T gr[3] = {T(0), T(0), T(0)}, J[3] = {T(0), T(0), T(0)};
+      T F[3], u[3], uu, pr;
+      macros3<P, NP>(a, gp, Cv, rho, gr, own.g, u, F, uu, pr);
+      collide3<P, NP, false, WALL>(a, nz, ph, Cv, rho, gr, J, own, u, F, uu, pr,
+                                   q, gx, gy, z);
+    }
+    __syncthreads();  // plane z - 1's slot is refilled next
+  }
 }
 
 template <int P, int NP>
@@ -452,6 +654,20 @@ cudaError_t launch_tile3_t(const Consts &c, const Grid &g, int cur, int mode,
   KArgs3<P> A;
   A.a = make_args<P>(c, g, cur, mode, o);
   A.nz = g.nz;
+  if constexpr (!NU) {
+    if (mode == MODE_STEP && g.march3) {
+      // slabs of z planes: enough CTAs to fill the GPU (~1216), at least 8
+      // planes per slab (each slab sums phi on two extra planes)
+      const int txy = tiles_x(g.nx) * ((g.ny + MY3 - 1) / MY3);
+      long long zl = ((long long)g.nz * txy + 1215) / 1216;
+      if (zl < 8) zl = 8;
+      if (zl > g.nz) zl = g.nz;
+      const int zlen = (int)zl;
+      dim3 grid(tiles_x(g.nx), (g.ny + MY3 - 1) / MY3, (g.nz + zlen - 1) / zlen);
+      march3_kernel<P, NP, WALL><<<grid, dim3(MX3, MY3), 0, s>>>(A, zlen);
+      return cudaGetLastError();
+    }
+  }
   constexpr int RC = NU ? 1 : 0, R = RC + 1;
   constexpr size_t smem = (size_t)NP * ((BX3 + 2 * R) * (BY3 + 2 * R) * (BZ3 + 2 * R) +
                                         (NU ? (BX3 + 2) * (BY3 + 2) * (BZ3 + 2) : 0)) *

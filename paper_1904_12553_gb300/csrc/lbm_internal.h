@@ -67,6 +67,7 @@ struct Grid {
   int *err;         // device error word (1: a bounded wait gave up)
   int grad_scheme;  // 0: central (Eq. N31a), 1: mixed (Eq. N40)
   bool use_tma;     // pipelined kernel usable for this grid
+  bool march3;      // D3Q15 step by the z-marching kernel
   TmaMaps tma[2];   // its descriptors, input buffer 0 or 1
 };
 

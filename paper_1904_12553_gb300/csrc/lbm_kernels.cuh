@@ -262,29 +262,29 @@ __device__ __forceinline__ void local_algebra(const KArgs<P> &a,
     rho = a.rho_base;
 #pragma unroll
     for (int i = 0; i < NP; ++i) hf[i] = f[i] - F * invN;
-    return;
-  }
-  T vp[NP];
+  } else {
+    T vp[NP];
 #pragma unroll
-  for (int j = 0; j < NP; ++j) vp[j] = a.off[j] + a.mul[j] * ph[j];
-  rho = a.rho_base;
+    for (int j = 0; j < NP; ++j) vp[j] = a.off[j] + a.mul[j] * ph[j];
+    rho = a.rho_base;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) rho += a.K[j] * vp[j];
-  T f[NP + 1];
+    for (int j = 0; j < NP; ++j) rho += a.K[j] * vp[j];
+    T f[NP + 1];
 #pragma unroll
-  for (int k = 0; k <= NP; ++k) {
-    T s = a.c0[k];
+    for (int k = 0; k <= NP; ++k) {
+      T s = a.c0[k];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) s += a.Q[k][j] * vp[j];
-    c[k] = s;
-    f[k] = s * (T(1) - s) * (T(1) - T(2) * s);
-  }
+      for (int j = 0; j < NP; ++j) s += a.Q[k][j] * vp[j];
+      c[k] = s;
+      f[k] = s * (T(1) - s) * (T(1) - T(2) * s);
+    }
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    T s = T(0);
+    for (int i = 0; i < NP; ++i) {
+      T s = T(0);
 #pragma unroll
-    for (int k = 0; k <= NP; ++k) s += a.Q[k][i] * f[k];
-    hf[i] = a.mul[i] * s;
+      for (int k = 0; k <= NP; ++k) s += a.Q[k][i] * f[k];
+      hf[i] = a.mul[i] * s;
+    }
   }
 }
 
