@@ -46,9 +46,9 @@ def alg_bytes_per_node(N: int, prec: str) -> int:
 
 # FP64 operations one node-step executes in the FP64 form at N=5 (ncu
 # instruction counts of the step kernel on the 1024x1024 droplets and
-# interfaces case, per node: 226 DFMA counted twice, 171.5 DADD, 132 DMUL;
+# interfaces case, per node: 187 DFMA counted twice, 180.5 DADD, 125 DMUL;
 # profiles/tile_kernel_fp64_n5_1024.md).
-FP64_FLOP_PER_NODE_N5 = 755.5
+FP64_FLOP_PER_NODE_N5 = 679.5
 # FP64 ALU peak derived from the GB300's unit counts and clock: 152 SMs x
 # 2 FP64 FMA lanes per SM per clock x 2 FLOP x 2070 MHz = 1.2586 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
