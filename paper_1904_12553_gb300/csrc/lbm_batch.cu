@@ -72,8 +72,8 @@ __device__ __forceinline__ void tile_step_body(const KArgs<P> &a, int x0, int y0
     NodeMac<P, NP> m;
     node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1, 0,
                                      0, g, m);
-    collide_stream<P, NP, false, WALL>(a, m, hreg, perr, g, pp, a.u_prev[q],
-                                       a.u_prev[V + q], gx, gy);
+    collide_stream<P, NP, false, WALL>(a, m, hreg, perr, g, pp, a.u_in[q],
+                                       a.u_in[V + q], gx, gy);
   }
   __syncthreads();  // sphi is reused by the next item
 }

@@ -189,7 +189,7 @@ Layout layout(const lbm_nphase_params *p) {
   L.hm = off;       off += 2 * align256(NP * QM * V * sS);
   L.gm = off;       off += 2 * align256(QM * V * sS);
   L.phi_prev = off; off += 2 * align256(NP * V * sT);
-  L.u_prev = off;   off += align256(D * V * sT);
+  L.u_prev = off;   off += 2 * align256(D * V * sT);
   L.stage = off;    off += align256((p->N + D) * V * 8);
   L.red = off;      off += align256(tiles * (p->N + 2) * 8);
   L.red_out = off;  off += align256(8 * 8);
@@ -487,7 +487,9 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   const size_t ppb = align256(n * g.V * sT);
   g.phi_prev[0] = base + L.phi_prev;
   g.phi_prev[1] = base + L.phi_prev + ppb;
-  g.u_prev = base + L.u_prev;
+  const size_t upb = align256((size_t)dims(p) * g.V * sT);
+  g.u_prev[0] = base + L.u_prev;
+  g.u_prev[1] = base + L.u_prev + upb;
   h->stage = (double *)(base + L.stage);
   g.red = (double *)(base + L.red);
   g.red_out = (double *)(base + L.red_out);
@@ -634,7 +636,7 @@ int state_parts(const lbm_nphase_t *h, Part out[5]) {
   out[1] = {h->g.hm[c], n * QM * V * sS};
   out[2] = {h->g.gm[c], QM * V * sS};
   out[3] = {h->g.phi_prev[c], n * V * sT};
-  out[4] = {h->g.u_prev, D * V * sT};
+  out[4] = {h->g.u_prev[c], D * V * sT};
   return 5;
 }
 }  // namespace

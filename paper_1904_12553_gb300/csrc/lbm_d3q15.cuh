@@ -41,7 +41,7 @@ static_assert(c3x(opp3(8)) == -c3x(8) && c3y(opp3(8)) == -c3y(8) &&
 constexpr int BX3 = 32, BY3 = 4, BZ3 = 2, NT3 = BX3 * BY3 * BZ3;
 
 template <int P> struct KArgs3 {
-  KArgs<P> a;  // pointers, constants (u_prev holds 3 planes)
+  KArgs<P> a;  // pointers, constants (u_in, u_out hold 3 planes)
   int nz;
 };
 
@@ -134,7 +134,7 @@ __device__ __forceinline__ void load_own3(const KArgs<P> &a, size_t q,
 #pragma unroll
   for (int k = 1; k < 15; ++k) o.g[k] = to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q));
 #pragma unroll
-  for (int d = 0; d < 3; ++d) o.up[d] = a.u_prev[(size_t)d * V + q];
+  for (int d = 0; d < 3; ++d) o.up[d] = a.u_in[(size_t)d * V + q];
 }
 
 // phi_i from a node's values in registers, summed in the order of node_phi3.
@@ -292,7 +292,7 @@ __device__ __forceinline__ void collide3(
     a.pp_out[(size_t)i * V + q] = ph[i];
   }
 #pragma unroll
-  for (int d = 0; d < 3; ++d) a.u_prev[(size_t)d * V + q] = u[d];
+  for (int d = 0; d < 3; ++d) a.u_out[(size_t)d * V + q] = u[d];
 }
 
 template <int P, int NP, bool NU, bool WALL>
@@ -583,7 +583,7 @@ __global__ void init3_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
       a.pp_out[(size_t)i * a.V + q] =
           (T)((2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN));
     }
-    for (int d = 0; d < 3; ++d) a.u_prev[(size_t)d * a.V + q] = u ? (T)u[(size_t)d * a.V + q] : T(0);
+    for (int d = 0; d < 3; ++d) a.u_out[(size_t)d * a.V + q] = u ? (T)u[(size_t)d * a.V + q] : T(0);
   }
 }
 
@@ -611,7 +611,7 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
     }
     T cc[NP + 1], rho, hf[NP];
     local_algebra<P, NP>(a, ph, cc, rho, hf);
-    const T u[3] = {a.u_prev[q], a.u_prev[V + q], a.u_prev[2 * V + q]};
+    const T u[3] = {a.u_out[q], a.u_out[V + q], a.u_out[2 * V + q]};
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T p0 = (T)p0d;
     for (int k = 1; k < 15; ++k) {

@@ -6,7 +6,7 @@
 //   hm[i][k-1][V]   moving populations h^i_k, k = 1..8
 //   gm[k-1][V]      NS populations g_k, k = 1..8 (g_0 never influences u, p
 //                   or phi: u has c_0 = 0 and Eq. N23 sums k >= 1)
-//   phi_prev[2][i][V]   phi_i(t-1) (Eq. N27), ping-pong; u_prev[2][V] in place
+//   phi_prev[2][i][V]   phi_i(t-1) (Eq. N27), ping-pong; u_prev[2][2][V] the same
 // The stored populations are post-streaming values at their node (push
 // scheme), so phi_i(x) = sum_k h^i_k(x) is local (Eq. N28).
 //
@@ -113,7 +113,8 @@ template <int P> struct alignas(16) KArgs {  // 16: bulk-copy granule
   Sm *hm_out, *gm_out;
   const T *pp_in;  // phi_prev at t-1
   T *pp_out;       // phi_prev for the next step (phi at t)
-  T *u_prev;
+  const T *u_in;   // u(t-1)
+  T *u_out;        // u(t) for the next step
   double *o_phi, *o_c, *o_u, *o_p, *o_rho, *red;
   int *err;
   int mode;
@@ -139,7 +140,8 @@ KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
   a.gm_out = (Sm *)g.gm[cur ^ 1];
   a.pp_in = (const T *)g.phi_prev[cur];
   a.pp_out = (T *)g.phi_prev[cur ^ 1];
-  a.u_prev = (T *)g.u_prev;
+  a.u_in = (const T *)g.u_prev[cur];
+  a.u_out = (T *)g.u_prev[cur ^ 1];
   a.o_phi = o.phi;
   a.o_c = o.c;
   a.o_u = o.u;
@@ -554,8 +556,8 @@ __device__ __forceinline__ void collide_stream(
     a.h0_out[(size_t)i * V + q] = rest;
     a.pp_out[(size_t)i * V + q] = ph;
   }
-  a.u_prev[q] = ux;
-  a.u_prev[V + q] = uy;
+  a.u_out[q] = ux;
+  a.u_out[V + q] = uy;
 }
 
 // Position of ring entry r of a (BX + 2R) x (BY + 2R) tile: top R rows,
@@ -732,8 +734,8 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   T pp[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) pp[i] = ldg(a.pp_in + (size_t)i * V + q);
-  collide_stream<P, NP, NU, WALL>(a, m, hreg, perr, g, pp, a.u_prev[q],
-                                  a.u_prev[V + q], gx, gy);
+  collide_stream<P, NP, NU, WALL>(a, m, hreg, perr, g, pp, a.u_in[q],
+                                  a.u_in[V + q], gx, gy);
 }
 
 // ---------------------------------------------------------------------------
@@ -922,8 +924,8 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
     const bool active = gx < nx && gy < ny;
     const size_t qn = (size_t)(active ? gy : 0) * nx + (active ? gx : 0);
     const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
-    const T upx = G::STAGE_U ? T(0) : a.u_prev[qn];
-    const T upy = G::STAGE_U ? T(0) : a.u_prev[a.V + qn];
+    const T upx = G::STAGE_U ? T(0) : a.u_in[qn];
+    const T upy = G::STAGE_U ? T(0) : a.u_in[a.V + qn];
     // A thread whose wait gave up still runs the phi sums below (on stale
     // shared data, harmlessly); the barrier after them makes the decision
     // to stop the same for the whole CTA.
@@ -1043,8 +1045,8 @@ __global__ void init_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
       const double ph = (2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN);
       a.pp_out[(size_t)i * a.V + q] = (T)ph;
     }
-    a.u_prev[q] = u ? (T)u[q] : T(0);
-    a.u_prev[a.V + q] = u ? (T)u[a.V + q] : T(0);
+    a.u_out[q] = u ? (T)u[q] : T(0);
+    a.u_out[a.V + q] = u ? (T)u[a.V + q] : T(0);
   }
 }
 
@@ -1076,7 +1078,7 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
     }
     T cc[NP + 1], rho, hf[NP];
     local_algebra<P, NP>(a, ph, cc, rho, hf);
-    const T ux = a.u_prev[q], uy = a.u_prev[V + q];
+    const T ux = a.u_out[q], uy = a.u_out[V + q];
     const T uu = ux * ux + uy * uy;
     const T p0 = (T)p0d;
 #pragma unroll
@@ -1213,7 +1215,7 @@ bool encode_tma_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
                 enc3(&m.h0, g.h0[b], sizeof(T), NP, G::WR, G::HB, NP) &&
                 enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HB, NP) &&
                 enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, G::TBY, 8) &&
-                enc3(&m.up, g.u_prev, sizeof(T), 2, BX, G::TBY, 2);
+                enc3(&m.up, g.u_prev[b], sizeof(T), 2, BX, G::TBY, 2);
       if (!ok) return false;
     }
     return true;
