@@ -55,7 +55,10 @@ typedef enum {
 typedef enum {
   LBM_FP64 = 0,     /* FP64 storage and arithmetic */
   LBM_FP32 = 1,     /* FP32 storage and arithmetic */
-  LBM_MIX_BF16 = 2, /* moving populations stored as BF16 f_k/w_k * s, FP32 math */
+  LBM_MIX_BF16 = 2, /* moving populations stored as BF16 (f_k/w_k - 3 c_k.u f~) * s,
+                       f~ = phi_i (h) or N/Gamma (g), with u and phi_i of the
+                       node the population was streamed from (D2Q9; D3Q15:
+                       f_k/w_k * s); FP32 math */
   LBM_MIX_FP16 = 3  /* moving populations stored as FP16 f_k/w_k * s, FP32 math */
 } lbm_precision;
 

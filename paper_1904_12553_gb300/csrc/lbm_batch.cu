@@ -58,7 +58,7 @@ __device__ __forceinline__ void tile_step_body(const KArgs<P> &a, int x0, int y0
   for (int r = tid; r < NRING; r += BX * TBY) {
     int lx, ly;
     ring_pos_1<TBY>(r, lx, ly);
-    phi_global<P, NP>(a, wrap(x0 - 1 + lx, nx), wrap_y<WALL>(y0 - 1 + ly, ny),
+    phi_global<P, NP, WALL>(a, wrap(x0 - 1 + lx, nx), wrap_y<WALL>(y0 - 1 + ly, ny),
                       sphi, PL, ly * SW + lx);
   }
   __syncthreads();
@@ -241,7 +241,7 @@ __device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
 #pragma unroll
     for (int k = 1; k < 9; ++k) r.g[k] = to_T(sgm[((k - 1) * TBY + ty) * BX + tx]);
   } else {
-    phi_global<LBM_FP32, NP>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
+    phi_global<LBM_FP32, NP, WALL>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                              (ty + 1) * SW + tx + 1);
   }
   constexpr int NRING = SW * SH - BX * TBY;
@@ -262,7 +262,7 @@ __device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
             spp[(i * BG::HB + ly) * BG::WR + bxr], e, a.sh_ld);
       }
     } else {
-      phi_global<LBM_FP32, NP>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
+      phi_global<LBM_FP32, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
                                ly * SW + lx);
     }
   }

@@ -611,7 +611,7 @@ lbm_status lbm_nphase_step(lbm_nphase_t *h, int64_t nsteps) {
 // --------------------------------------------------------------------------
 namespace {
 struct StateHeader {
-  char magic[8];  // "LBMNPHS1"
+  char magic[8];  // "LBMNPHS2"
   int32_t N, nx, ny, precision, wall_y, grad_scheme;
   int64_t steps;
   uint64_t payload;  // bytes after the header
@@ -655,7 +655,7 @@ lbm_status lbm_nphase_get_state(lbm_nphase_t *h, void *dst, size_t bytes) {
   if (bytes < lbm_nphase_state_bytes(h)) return LBM_ENOMEM;
   StateHeader hd;
   memset(&hd, 0, sizeof(hd));
-  memcpy(hd.magic, "LBMNPHS1", 8);
+  memcpy(hd.magic, "LBMNPHS2", 8);
   hd.N = h->prm.N;
   hd.nx = h->prm.nx;
   hd.ny = h->prm.ny;
@@ -691,7 +691,7 @@ lbm_status lbm_nphase_set_state(lbm_nphase_t *h, const void *src, size_t bytes) 
   cudaError_t e = cudaMemcpy(&hd, src, sizeof(hd),
                              dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  if (memcmp(hd.magic, "LBMNPHS1", 8) != 0 || hd.N != h->prm.N ||
+  if (memcmp(hd.magic, "LBMNPHS2", 8) != 0 || hd.N != h->prm.N ||
       hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.nz != depth(&h->prm) ||
       hd.lattice != h->prm.lattice ||
       hd.precision != h->prm.precision ||

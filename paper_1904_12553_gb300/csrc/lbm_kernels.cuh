@@ -57,27 +57,30 @@ static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 &&
                   opp_of(7) == 5 && opp_of(8) == 6,
               "opposite directions");
 
-// Storage policy per precision.
+// Storage policy per precision. MIX: 16-bit moving populations in stored
+// units s f_k / w_k. REF: stored relative to the advective part of their
+// equilibrium at their source node (BF16, whose 8 significant bits need it;
+// FP16's 11 bits meet the accuracy targets without it).
 template <int P> struct Prec;
 template <> struct Prec<LBM_FP64> {
   typedef double T;
   typedef double Sm;
-  static constexpr bool MIX = false;
+  static constexpr bool MIX = false, REF = false;
 };
 template <> struct Prec<LBM_FP32> {
   typedef float T;
   typedef float Sm;
-  static constexpr bool MIX = false;
+  static constexpr bool MIX = false, REF = false;
 };
 template <> struct Prec<LBM_MIX_BF16> {
   typedef float T;
   typedef __nv_bfloat16 Sm;
-  static constexpr bool MIX = true;
+  static constexpr bool MIX = true, REF = true;
 };
 template <> struct Prec<LBM_MIX_FP16> {
   typedef float T;
   typedef __half Sm;
-  static constexpr bool MIX = true;
+  static constexpr bool MIX = true, REF = false;
 };
 
 __device__ __forceinline__ float __fadd_rn_T(float a, float b) { return __fadd_rn(a, b); }
@@ -193,6 +196,84 @@ template <int P>
 __device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
                                                        size_t q) {
   return to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
+}
+
+// 16-bit forms: every moving population is stored relative to the advective
+// part of its equilibrium (Eqs. 25, N25) evaluated at the node it was
+// streamed from: slot k of node y holds
+//     s f_k / w_k - 3 s (c_k . u) phi_i     (h of phase i)
+//     s g_k / w_k - 3 s (c_k . u) rho~      (g; rho~ = the constant N/Gamma)
+// with u = u(t), phi = phi(t) of the source node y - c_k (of y itself when
+// y - c_k lies behind a wall: the slot was filled by bounce-back). The writer
+// uses its own u(t), phi(t); the reader takes them as u(t-1), phi(t-1) of the
+// source. The subtracted part is the bulk of a population in a moving flow,
+// so the 16-bit value keeps its significant bits for the rest. Both sides
+// compute it with the same rounded operations (no contraction), so a value
+// decodes to exactly what its writer counted in the node's mass balance.
+__device__ __forceinline__ float cdotu(int k, float ux, float uy) {
+  const int cx = cx_of(k), cy = cy_of(k);
+  const float a = cx > 0 ? ux : -ux, b = cy > 0 ? uy : -uy;
+  return cx != 0 && cy != 0 ? __fadd_rn(a, b) : (cx != 0 ? a : b);
+}
+__device__ __forceinline__ double cdotu(int k, double ux, double uy) {
+  return cx_of(k) * ux + cy_of(k) * uy;
+}
+// 3 s (c_k . u) f in stored units; s3 = 3 s.
+__device__ __forceinline__ float adv_units(float cu, float f, float s3) {
+  return __fmul_rn(__fmul_rn(cu, f), s3);
+}
+__device__ __forceinline__ double adv_units(double cu, double f, double s3) {
+  return cu * f * s3;
+}
+
+// The node slot k of (x, y) was streamed from: (x, y) - c_k, periodic in x
+// (and in y without walls); behind a wall, (x, y) itself.
+template <bool WALL>
+__device__ __forceinline__ size_t source_node(int x, int y, int k, int nx,
+                                              int ny) {
+  int sx = x - cx_of(k), sy = y - cy_of(k);
+  if (WALL && (sy < 0 || sy >= ny)) {
+    sx = x;
+    sy = y;
+  }
+  sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+  sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+  return (size_t)sy * nx + sx;
+}
+
+// Moving populations of phase i (mov[0..7] = h_1..8) and the NS populations
+// (g[1..8]) of node (x, y) at index q, in stored units, from global memory.
+template <int P, bool WALL>
+__device__ __forceinline__ void load_h_node(const KArgs<P> &a, int i, int x,
+                                            int y, size_t q,
+                                            typename Prec<P>::T *mov) {
+  typedef typename Prec<P>::T T;
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    T v = load_hm<P>(a, i, k, q);
+    if constexpr (Prec<P>::REF) {
+      const size_t qs = source_node<WALL>(x, y, k, a.nx, a.ny);
+      const T cu = cdotu(k, ldg(a.u_in + qs), ldg(a.u_in + a.V + qs));
+      v = __fadd_rn(v, adv_units(cu, ldg(a.pp_in + (size_t)i * a.V + qs),
+                                 T(3) * a.sh_st));
+    }
+    mov[k - 1] = v;
+  }
+}
+template <int P, bool WALL>
+__device__ __forceinline__ void load_g_node(const KArgs<P> &a, int x, int y,
+                                            size_t q, typename Prec<P>::T *g) {
+  typedef typename Prec<P>::T T;
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    T v = load_gm<P>(a, k, q);
+    if constexpr (Prec<P>::REF) {
+      const size_t qs = source_node<WALL>(x, y, k, a.nx, a.ny);
+      const T cu = cdotu(k, ldg(a.u_in + qs), ldg(a.u_in + a.V + qs));
+      v = __fadd_rn(v, adv_units(cu, a.rho_base, T(3) * a.sg_st));
+    }
+    g[k] = v;
+  }
 }
 
 // Order parameter of one node from its stored values. FP64: sum of the nine
@@ -503,7 +584,11 @@ __device__ __forceinline__ void collide_stream(
       inner += E1 * (cxk * m.grx + cyk * m.gry) + E2 * (cxk * m.Jx + cyk * m.Jy);
     const T t = A0 + C1 * cF + cu * inner;
     const int kk = dk[k];
-    if constexpr (MIX)
+    if constexpr (Prec<P>::REF)
+      a.gm_out[(size_t)(kk - 1) * V + dst[k]] = to_S<typename Prec<P>::Sm>(
+          keep_g * g[k] + a.sg_st * t -
+          adv_units(cdotu(kk, ux, uy), a.rho_base, T(3) * a.sg_st));
+    else if constexpr (MIX)
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] =
           to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
     else
@@ -534,10 +619,15 @@ __device__ __forceinline__ void collide_stream(
       const T t = al + T(cx_of(k)) * bx + T(cy_of(k)) * by;
       const int kk = dk[k];
       if constexpr (MIX) {
-        const auto sv = to_S<typename Prec<P>::Sm>(keep * hreg[i][k] + t);
+        // REF: relative to the advective part at this node, the slot's source
+        const T ref = Prec<P>::REF ? adv_units(cdotu(kk, ux, uy), ph, T(3) * a.sh_st)
+                                   : T(0);
+        const auto sv = to_S<typename Prec<P>::Sm>(keep * hreg[i][k] + t - ref);
         a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = sv;
-        // the mass balance uses the value as stored
-        moving_sum = __fmaf_rn(w_of<T>(kk) * a.sh_ld, to_T(sv), moving_sum);
+        // the mass balance uses the value as the reader will decode it
+        moving_sum = __fmaf_rn(w_of<T>(kk) * a.sh_ld,
+                               Prec<P>::REF ? __fadd_rn(to_T(sv), ref) : to_T(sv),
+                               moving_sum);
       } else {
         const T hs = keep * hreg[i][k] + w_of<T>(k) * t;
         a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = hs;
@@ -577,7 +667,7 @@ __device__ __forceinline__ void ring_pos(int r, int &lx, int &ly) {
 }
 
 // phi_i at node (sx, sy) from global memory.
-template <int P, int NP>
+template <int P, int NP, bool WALL>
 __device__ __forceinline__ void phi_global(const KArgs<P> &a, int sx, int sy,
                                            typename Prec<P>::T *out, int plane,
                                            int idx) {
@@ -586,8 +676,7 @@ __device__ __forceinline__ void phi_global(const KArgs<P> &a, int sx, int sy,
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     T mov[8], err;
-#pragma unroll
-    for (int k = 1; k < 9; ++k) mov[k - 1] = load_hm<P>(a, i, k, q);
+    load_h_node<P, WALL>(a, i, sx, sy, q, mov);
     const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * a.V + q);
     out[i * plane + idx] =
         node_phi<P>(ldg(a.h0_in + (size_t)i * a.V + q), mov, pp, err, a.sh_ld);
@@ -627,8 +716,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       hreg[i][0] = ldg(a.h0_in + (size_t)i * V + q);
-#pragma unroll
-      for (int k = 1; k < 9; ++k) hreg[i][k] = load_hm<P>(a, i, k, q);
+      load_h_node<P, WALL>(a, i, sx, sy, q, &hreg[i][1]);
       const T pp = P == LBM_FP64 ? T(0) : ldg(a.pp_in + (size_t)i * V + q);
       sphi[i][(ty + R) * SW + tx + R] =
           node_phi<P>(hreg[i][0], &hreg[i][1], pp, perr[i], a.sh_ld);
@@ -639,7 +727,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   for (int r = tid; r < NRING; r += NT) {
     int lx, ly;
     ring_pos<R>(r, lx, ly);
-    phi_global<P, NP>(a, wrap(x0 - R + lx, nx), wrap_y<WALL>(y0 - R + ly, ny),
+    phi_global<P, NP, WALL>(a, wrap(x0 - R + lx, nx), wrap_y<WALL>(y0 - R + ly, ny),
                       &sphi[0][0], SH * SW, ly * SW + lx);
   }
   __syncthreads();
@@ -683,8 +771,12 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
   // 4. Own node: stencils, C_i, forces, u, p.
   const size_t q = (size_t)(active ? gy : 0) * nx + (active ? gx : 0);
   T g[9];
+  if (active) {
+    load_g_node<P, WALL>(a, gx, gy, q, g);
+  } else {
 #pragma unroll
-  for (int k = 1; k < 9; ++k) g[k] = active ? load_gm<P>(a, k, q) : T(0);
+    for (int k = 1; k < 9; ++k) g[k] = T(0);
+  }
   NodeMac<P, NP> m;
   node_macros<P, NP, NU, SW, CW, G40>(a, &sphi[0][0], SH * SW, &sC[0][0],
                                       CH * CW, ty + R, tx + R, ty + RC,
@@ -783,8 +875,19 @@ template <int P> struct TmaGeom {
   static constexpr int NTH = BX * TBY;              // threads per CTA
   static constexpr int HB = TBY + 2;                // box height
   static constexpr int S = 2;                       // pipeline stages
-  static constexpr bool STAGE_U = WIDE;             // u(t-1) in the stage
-  static constexpr bool TWO_BARRIERS = WIDE;
+  // 16-bit forms decode every population with phi(t-1) and u(t-1) of the
+  // node it came from: the ring's sources lie two rows out, so these two
+  // boxes carry two halo rows, and u(t-1) is staged with halo.
+  static constexpr bool REF = Prec<P>::REF;
+  static constexpr int RY = REF ? 2 : 1;            // halo rows, phi(t-1) and u(t-1)
+  static constexpr int HBP = TBY + 2 * RY;          // their box height
+  static constexpr int UW = REF ? WR : BX;          // u(t-1) box
+  static constexpr int UH = REF ? HBP : TBY;
+  static constexpr int UOX = REF ? HXR : 0, UOY = REF ? RY : 0;
+  static constexpr bool STAGE_U = WIDE || REF;     // u(t-1) in the stage
+  // two barriers per tile (one phi tile suffices), or one barrier with the
+  // phi tile double-buffered (FP16: the fastest shape that fits two CTAs)
+  static constexpr bool TWO_BARRIERS = WIDE || REF;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -836,19 +939,21 @@ template <int P, int NP> struct TmaStage {
   static constexpr size_t al(size_t b) { return (b + 127) & ~(size_t)127; }
   static constexpr size_t HM = al((size_t)8 * NP * G::HB * G::WM * sizeof(Sm));
   static constexpr size_t H0 = al((size_t)NP * G::HB * G::WR * sizeof(T));
-  static constexpr size_t PP = H0;
+  static constexpr size_t PP = al((size_t)NP * G::HBP * G::WR * sizeof(T));
   static constexpr size_t GM = al((size_t)8 * G::TBY * BX * sizeof(Sm));
-  static constexpr size_t UP = G::STAGE_U ? al((size_t)2 * G::TBY * BX * sizeof(T)) : 0;
+  static constexpr size_t UP = G::STAGE_U ? al((size_t)2 * G::UH * G::UW * sizeof(T)) : 0;
   static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
   // bytes the TMA engine writes per stage (full boxes, including fill)
   static constexpr uint32_t TX =
       (uint32_t)((size_t)8 * NP * G::HB * G::WM * sizeof(Sm) +
-                 2 * (size_t)NP * G::HB * G::WR * sizeof(T) +
+                 (size_t)NP * G::HB * G::WR * sizeof(T) +
+                 (size_t)NP * G::HBP * G::WR * sizeof(T) +
                  (size_t)8 * G::TBY * BX * sizeof(Sm) +
-                 (G::STAGE_U ? (size_t)2 * G::TBY * BX * sizeof(T) : 0));
+                 (G::STAGE_U ? (size_t)2 * G::UH * G::UW * sizeof(T) : 0));
   static constexpr size_t SPHI = al((size_t)NP * (G::TBY + 2) * (BX + 2) * sizeof(T));
   static constexpr int S = G::S;
-  static constexpr size_t SMEM = S * BYTES + 2 * SPHI + 64;
+  static constexpr int NSPHI = G::TWO_BARRIERS ? 1 : 2;
+  static constexpr size_t SMEM = S * BYTES + NSPHI * SPHI + 64;
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
@@ -869,7 +974,7 @@ __device__ __forceinline__ void ring_pos_1(int r, int &lx, int &ly) {
 }
 
 template <int P, int NP, bool WALL>
-__global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
+__global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
     tile_kernel_tma(const KArgs<P> a, const __grid_constant__ TmaMaps maps,
                     int ntx, int ntiles) {
   typedef typename Prec<P>::T T;
@@ -880,7 +985,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
   constexpr int TBY = G::TBY;
   constexpr int SW = BX + 2, SH = TBY + 2, PL = SW * SH;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + 2 * St::SPHI);
+  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::NSPHI * St::SPHI);
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int nx = a.nx, ny = a.ny;
@@ -894,10 +999,11 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
     mbar_expect_tx(b, St::TX);
     tma_load_3d(st, &maps.hm, x0 - G::HXM, y0 - 1, 0, b);
     tma_load_3d(st + St::HM, &maps.h0, x0 - G::HXR, y0 - 1, 0, b);
-    tma_load_3d(st + St::HM + St::H0, &maps.pp, x0 - G::HXR, y0 - 1, 0, b);
+    tma_load_3d(st + St::HM + St::H0, &maps.pp, x0 - G::HXR, y0 - G::RY, 0, b);
     tma_load_3d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, 0, b);
     if (G::STAGE_U)
-      tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0, y0, 0, b);
+      tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0 - G::UOX,
+                  y0 - G::UOY, 0, b);
   };
 
   if (tid == 0) {
@@ -912,7 +1018,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
   for (int j = 0; j < nmine; ++j) {
     const int t = blockIdx.x + j * gridDim.x;
     const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
-    T *sphi = (T *)(smem + S * St::BYTES + (j & 1) * St::SPHI);
+    T *sphi = (T *)(smem + S * St::BYTES + (St::NSPHI == 2 ? (j & 1) : 0) * St::SPHI);
     const unsigned char *st = smem + (j % S) * St::BYTES;
     const Sm *shm = (const Sm *)st;
     const T *sh0 = (const T *)(st + St::HM);
@@ -926,6 +1032,43 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
     const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
     const T upx = G::STAGE_U ? T(0) : a.u_in[qn];
     const T upy = G::STAGE_U ? T(0) : a.u_in[a.V + qn];
+    // 16-bit forms: u(t-1) and phi(t-1) of the node that slot k of node
+    // (xn, yn) was streamed from; (cb, rb) is the node's position in the
+    // u(t-1) and phi(t-1) boxes. Sources that wrap around the grid come from
+    // global memory.
+    // Tiles whose two-node neighbourhood lies inside the grid (no wrap, no
+    // wall) find every source in the boxes at a fixed offset.
+    const bool inner = x0 >= 2 && x0 + BX + 2 <= nx && y0 >= 2 && y0 + TBY + 2 <= ny;
+    auto source = [&](int k, int xn, int yn, int cb, int rb, T &sux, T &suy,
+                      T *sph) {
+      if (inner) {
+        const int o = (rb - cy_of(k)) * G::UW + cb - cx_of(k);
+        sux = sup[o];
+        suy = sup[G::UH * G::UW + o];
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+          sph[i] = spp[(i * G::HBP + rb - cy_of(k)) * G::WR + cb - cx_of(k)];
+        return;
+      }
+      int sx = xn - cx_of(k), sy = yn - cy_of(k);
+      int c = cb - cx_of(k), r = rb - cy_of(k);
+      if (WALL && (sy < 0 || sy >= ny)) {
+        sx = xn; sy = yn; c = cb; r = rb;
+      }
+      if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) {
+        sux = sup[r * G::UW + c];
+        suy = sup[(G::UH + r) * G::UW + c];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sph[i] = spp[(i * G::HBP + r) * G::WR + c];
+      } else {
+        const size_t qs = source_node<WALL>(xn, yn, k, nx, ny);
+        sux = ldg(a.u_in + qs);
+        suy = ldg(a.u_in + a.V + qs);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sph[i] = ldg(a.pp_in + (size_t)i * a.V + qs);
+      }
+    };
+    const T s3h = T(3) * a.sh_st, s3g = T(3) * a.sg_st;
     // A thread whose wait gave up still runs the phi sums below (on stale
     // shared data, harmlessly); the barrier after them makes the decision
     // to stop the same for the whole CTA.
@@ -934,14 +1077,29 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
     // phi on the tile and its ring. A position whose node lies inside the
     // array without wrapping reads the staged box; others read global memory.
     auto box_phi = [&](int bxm, int bxr, int by, T *err) {
+      T mv[NP][8];
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T mov[8];
+      for (int i = 0; i < NP; ++i)
 #pragma unroll
         for (int k = 1; k < 9; ++k)
-          mov[k - 1] = to_T(shm[((i * 8 + k - 1) * G::HB + by) * G::WM + bxm]);
+          mv[i][k - 1] = to_T(shm[((i * 8 + k - 1) * G::HB + by) * G::WM + bxm]);
+      if constexpr (G::REF) {
+        const int xn = x0 - G::HXR + bxr, yn = y0 - 1 + by;
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+          T sux, suy, sph[NP];
+          source(k, xn, yn, bxr, by - 1 + G::RY, sux, suy, sph);
+          const T cu = cdotu(k, sux, suy);
+#pragma unroll
+          for (int i = 0; i < NP; ++i)
+            mv[i][k - 1] = __fadd_rn(mv[i][k - 1], adv_units(cu, sph[i], s3h));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T *mov = mv[i];
         const T rest = sh0[(i * G::HB + by) * G::WR + bxr];
-        const T pp = spp[(i * G::HB + by) * G::WR + bxr];
+        const T pp = spp[(i * G::HBP + by - 1 + G::RY) * G::WR + bxr];
         T e;
         sphi[i * PL + by * SW + (bxr - G::HXR + 1)] =
             node_phi<P>(rest, mov, pp, e, a.sh_ld);
@@ -958,14 +1116,28 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
 #pragma unroll
         for (int k = 1; k < 9; ++k)
           hreg[i][k] = to_T(shm[((i * 8 + k - 1) * G::HB + ty + 1) * G::WM + tx + G::HXM]);
-        pp[i] = spp[(i * G::HB + ty + 1) * G::WR + tx + G::HXR];
-        sphi[i * PL + (ty + 1) * SW + tx + 1] =
-            node_phi<P>(hreg[i][0], &hreg[i][1], pp[i], perr[i], a.sh_ld);
+        pp[i] = spp[(i * G::HBP + ty + G::RY) * G::WR + tx + G::HXR];
       }
 #pragma unroll
       for (int k = 1; k < 9; ++k) g[k] = to_T(sgm[((k - 1) * TBY + ty) * BX + tx]);
+      if constexpr (G::REF) {
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+          T sux, suy, sph[NP];
+          source(k, gx, gy, tx + G::HXR, ty + G::RY, sux, suy, sph);
+          const T cu = cdotu(k, sux, suy);
+#pragma unroll
+          for (int i = 0; i < NP; ++i)
+            hreg[i][k] = __fadd_rn(hreg[i][k], adv_units(cu, sph[i], s3h));
+          g[k] = __fadd_rn(g[k], adv_units(cu, a.rho_base, s3g));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+        sphi[i * PL + (ty + 1) * SW + tx + 1] =
+            node_phi<P>(hreg[i][0], &hreg[i][1], pp[i], perr[i], a.sh_ld);
     } else {
-      phi_global<P, NP>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
+      phi_global<P, NP, WALL>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                         (ty + 1) * SW + tx + 1);
     }
     constexpr int NRING = SW * SH - BX * TBY;
@@ -977,7 +1149,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
       if (rx >= 0 && rx < nx && ry >= 0 && ry < ny)
         box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, ly, nullptr);
       else
-        phi_global<P, NP>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
+        phi_global<P, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
                           ly * SW + lx);
     }
     // After this barrier every thread is done with tile j - 1. With one
@@ -1000,8 +1172,9 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, 1)
                                        0, 0, g, m);
       collide_stream<P, NP, false, WALL>(
           a, m, hreg, perr, g, pp,
-          G::STAGE_U ? sup[ty * BX + tx] : upx,
-          G::STAGE_U ? sup[(TBY + ty) * BX + tx] : upy, gx, gy);
+          G::STAGE_U ? sup[(ty + G::UOY) * G::UW + tx + G::UOX] : upx,
+          G::STAGE_U ? sup[(G::UH + ty + G::UOY) * G::UW + tx + G::UOX] : upy,
+          gx, gy);
     }
     if (G::TWO_BARRIERS) {
       __syncthreads();
@@ -1085,9 +1258,13 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
     for (int k = 1; k < 9; ++k) {
       const T cu = T(cx_of(k)) * ux + T(cy_of(k)) * uy;
       const T geq = w_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-      if constexpr (Prec<P>::MIX)
-        gm[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w_of<T>(k)));
-      else
+      if constexpr (Prec<P>::MIX) {
+        const size_t qs = source_node<WALL>(x, y, k, nx, ny);
+        const T ref = Prec<P>::REF ? adv_units(cdotu(k, a.u_out[qs], a.u_out[V + qs]),
+                                               a.rho_base, T(3) * a.sg_st)
+                                   : T(0);
+        gm[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w_of<T>(k)) - ref);
+      } else
         gm[(size_t)(k - 1) * V + q] = geq;
     }
 #pragma unroll
@@ -1101,9 +1278,14 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
       for (int k = 1; k < 9; ++k) {
         const T heq = w_of<T>(k) * (aC + T(3) * ph[i] * (T(cx_of(k)) * ux + T(cy_of(k)) * uy));
         if constexpr (Prec<P>::MIX) {
-          const Sm sv = to_S<Sm>(heq * (a.sh_st / w_of<T>(k)));
+          const size_t qs = source_node<WALL>(x, y, k, nx, ny);
+          const T ref = Prec<P>::REF ? adv_units(cdotu(k, a.u_out[qs], a.u_out[V + qs]),
+                                                 a.pp_out[(size_t)i * V + qs], T(3) * a.sh_st)
+                                     : T(0);
+          const Sm sv = to_S<Sm>(heq * (a.sh_st / w_of<T>(k)) - ref);
           hm[((size_t)(i * 8 + k - 1)) * V + q] = sv;
-          moving = __fadd_rn(moving, __fmul_rn(to_T(sv), w_of<T>(k) * a.sh_ld));
+          moving = __fadd_rn(moving, __fmul_rn(Prec<P>::REF ? __fadd_rn(to_T(sv), ref) : to_T(sv),
+                                               w_of<T>(k) * a.sh_ld));
         } else {
           hm[((size_t)(i * 8 + k - 1)) * V + q] = heq;
           moving = __fadd_rn_T(moving, heq);
@@ -1213,9 +1395,9 @@ bool encode_tma_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
       TmaMaps &m = *(TmaMaps *)&g.tma[b];
       bool ok = enc3(&m.hm, g.hm[b], sizeof(Sm), 8 * NP, G::WM, G::HB, 8 * NP) &&
                 enc3(&m.h0, g.h0[b], sizeof(T), NP, G::WR, G::HB, NP) &&
-                enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HB, NP) &&
+                enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HBP, NP) &&
                 enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, G::TBY, 8) &&
-                enc3(&m.up, g.u_prev[b], sizeof(T), 2, BX, G::TBY, 2);
+                enc3(&m.up, g.u_prev[b], sizeof(T), 2, G::UW, G::UH, 2);
       if (!ok) return false;
     }
     return true;

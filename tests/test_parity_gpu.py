@@ -225,12 +225,11 @@ def test_precision_forms_error(prec):
 
 
 # max |dphi|, max |du| / max |u|, centre-of-mass shift (nodes) allowed
-# after 2000 steps of the 512x512 collision. BF16 keeps 8 significant bits
-# of populations dominated by the advective part 3 c.(phi u) of their
-# equilibrium, and misses the 1e-3 target here (measured 1.3e-2, 1.8e-2 and
-# 0.10 nodes); FP32 and FP16 meet it.
+# after 2000 steps of the 512x512 collision. FP32 and FP16 meet the 1e-3
+# target on phi. BF16 (8 significant bits, populations stored relative to
+# the advective part of their equilibrium) measures 1.1e-3: just above it.
 COLLISION_BOUNDS = {"fp32": (1e-3, 1e-3, 1e-2), "fp16": (1e-3, 5e-3, 1e-2),
-                    "bf16": (2e-2, 3e-2, 0.2)}
+                    "bf16": (1.5e-3, 1e-2, 5e-2)}
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
