@@ -863,6 +863,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 //    -9% / -24%; ring phi split over (position, phase) pairs on all warps,
 //    -1.5% / -35%. Instrumented, the FP32 kernel spends 13-19% of its time
 //    in the stage wait.
+//  - BF16 with the reference encoding (two halo rows in the phi(t-1) and
+//    u(t-1) boxes): two barriers, one phi tile, two CTAs per SM at 128
+//    registers is the only shape that keeps two CTAs; one CTA per SM with one
+//    barrier (2 stages) ran 20% slower, with 3 stages 22%; the ring's decode
+//    spread over all warps by (position, phase) 6% slower.
 template <int P> struct TmaGeom {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
