@@ -59,7 +59,7 @@ typedef enum {
                        f~ = phi_i (h) or N/Gamma (g), with u and phi_i of the
                        node the population was streamed from (D2Q9; D3Q15:
                        f_k/w_k * s); FP32 math */
-  LBM_MIX_FP16 = 3  /* moving populations stored as FP16 f_k/w_k * s, FP32 math */
+  LBM_MIX_FP16 = 3  /* the same with FP16 storage; FP32 math */
 } lbm_precision;
 
 /* Model parameters, as the paper states them (Sections 2-4). */

