@@ -843,32 +843,27 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 // Halo positions that wrap around the domain (periodic edges, wall ghost
 // rows, ragged tails) are summed from global memory instead.
 // ---------------------------------------------------------------------------
-// Pipeline shape per storage form, chosen by timing the N=5 2048^2 step on
-// GB300:
-//  - FP32: 2 stages (160 KB, one CTA per SM), u(t-1) staged with the tile,
-//    two barriers per tile (the stage is refilled right after the tile, so
-//    the next-but-one tile loads during a whole tile). A third stage needs
-//    227 KB and leaves ~28 KB of L1: 28% slower; one barrier per tile: 23%
-//    slower; one stage with two CTAs per SM: 15% slower.
-//  - 16-bit: 2 stages (106 KB, two CTAs per SM at <= 128 registers), u(t-1)
-//    loaded directly, one barrier per tile (stage j-1 refilled after the phi
-//    barrier of tile j, phi tile double-buffered). 3 stages with one CTA per
-//    SM: 6% slower; 4 stages: 12% slower.
-//  - Tile height 8: FP32 with 32 x 12 tiles (384 threads, 225 KB) ran 30%
-//    slower; a stage without halo columns (wrapped ring columns from global
-//    memory, two CTAs per SM) ran 48% slower.
-//  - Also measured and rejected (FP32 / 16-bit): g and u(t-1) loaded from
-//    global memory before the wait instead of staged, -19% (and a third
-//    stage on top of that, a further -6%); releasing the stage right after
-//    the phi barrier (u(t-1) read into registers, one barrier per tile),
-//    -9% / -24%; ring phi split over (position, phase) pairs on all warps,
-//    -1.5% / -35%. Instrumented, the FP32 kernel spends 13-19% of its time
-//    in the stage wait.
-//  - BF16 with the reference encoding (two halo rows in the phi(t-1) and
-//    u(t-1) boxes): two barriers, one phi tile, two CTAs per SM at 128
-//    registers is the only shape that keeps two CTAs; one CTA per SM with one
-//    barrier (2 stages) ran 20% slower, with 3 stages 22%; the ring's decode
-//    spread over all warps by (position, phase) 6% slower.
+// Pipeline shape, chosen by timing the N=5 2048^2 step on GB300: 2 stages,
+// u(t-1) staged with the tile, two barriers per tile (the stage is refilled
+// right after the tile, so the next-but-one tile loads during a whole tile;
+// one phi tile suffices). FP32: 154 KB, one CTA per SM. 16-bit forms (their
+// populations decoded with phi(t-1) and u(t-1) of the source node: those two
+// boxes carry two halo rows): 111 KB and 128 registers, two CTAs per SM.
+// Measured and rejected:
+//  - FP32: a third stage (227 KB, ~28 KB of L1 left) -28%; one barrier per
+//    tile -23%; one stage with two CTAs per SM -15%; 32 x 12 tiles (384
+//    threads, 225 KB) -30%; a stage without halo columns (wrapped ring
+//    columns from global memory, two CTAs per SM) -48%; g and u(t-1) loaded
+//    from global memory before the wait instead of staged -19% (a third
+//    stage on top, a further -6%); releasing the stage after the phi
+//    barrier (one barrier per tile) -9%; the ring's phi split over
+//    (position, phase) pairs on all warps -1.5%. Instrumented, the kernel
+//    spends 13-19% of its time in the stage wait.
+//  - 16-bit with the source-relative encoding: one CTA per SM with one
+//    barrier and a double-buffered phi tile -20% (3 stages -22%); the ring's
+//    decode spread over all warps -6%. With plain scaled storage (an earlier
+//    form: 2 stages, direct u(t-1), one barrier, two CTAs) the 16-bit step
+//    ran 35% faster but missed the accuracy targets.
 template <int P> struct TmaGeom {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
@@ -885,15 +880,12 @@ template <int P> struct TmaGeom {
   // node it came from: the ring's sources lie two rows out, so these two
   // boxes carry two halo rows, and u(t-1) is staged with halo.
   static constexpr bool REF = Prec<P>::REF;
+  static_assert(WIDE || REF, "16-bit storage is source-relative");
   static constexpr int RY = REF ? 2 : 1;            // halo rows, phi(t-1) and u(t-1)
   static constexpr int HBP = TBY + 2 * RY;          // their box height
   static constexpr int UW = REF ? WR : BX;          // u(t-1) box
   static constexpr int UH = REF ? HBP : TBY;
   static constexpr int UOX = REF ? HXR : 0, UOY = REF ? RY : 0;
-  static constexpr bool STAGE_U = WIDE || REF;     // u(t-1) in the stage
-  // two barriers per tile (one phi tile suffices), or one barrier with the
-  // phi tile double-buffered (FP16: the fastest shape that fits two CTAs)
-  static constexpr bool TWO_BARRIERS = WIDE || REF;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -947,7 +939,7 @@ template <int P, int NP> struct TmaStage {
   static constexpr size_t H0 = al((size_t)NP * G::HB * G::WR * sizeof(T));
   static constexpr size_t PP = al((size_t)NP * G::HBP * G::WR * sizeof(T));
   static constexpr size_t GM = al((size_t)8 * G::TBY * BX * sizeof(Sm));
-  static constexpr size_t UP = G::STAGE_U ? al((size_t)2 * G::UH * G::UW * sizeof(T)) : 0;
+  static constexpr size_t UP = al((size_t)2 * G::UH * G::UW * sizeof(T));
   static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
   // bytes the TMA engine writes per stage (full boxes, including fill)
   static constexpr uint32_t TX =
@@ -955,11 +947,10 @@ template <int P, int NP> struct TmaStage {
                  (size_t)NP * G::HB * G::WR * sizeof(T) +
                  (size_t)NP * G::HBP * G::WR * sizeof(T) +
                  (size_t)8 * G::TBY * BX * sizeof(Sm) +
-                 (G::STAGE_U ? (size_t)2 * G::UH * G::UW * sizeof(T) : 0));
+                 (size_t)2 * G::UH * G::UW * sizeof(T));
   static constexpr size_t SPHI = al((size_t)NP * (G::TBY + 2) * (BX + 2) * sizeof(T));
   static constexpr int S = G::S;
-  static constexpr int NSPHI = G::TWO_BARRIERS ? 1 : 2;
-  static constexpr size_t SMEM = S * BYTES + NSPHI * SPHI + 64;
+  static constexpr size_t SMEM = S * BYTES + SPHI + 64;
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
@@ -991,7 +982,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
   constexpr int TBY = G::TBY;
   constexpr int SW = BX + 2, SH = TBY + 2, PL = SW * SH;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::NSPHI * St::SPHI);
+  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::SPHI);
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int nx = a.nx, ny = a.ny;
@@ -1007,9 +998,8 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
     tma_load_3d(st + St::HM, &maps.h0, x0 - G::HXR, y0 - 1, 0, b);
     tma_load_3d(st + St::HM + St::H0, &maps.pp, x0 - G::HXR, y0 - G::RY, 0, b);
     tma_load_3d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, 0, b);
-    if (G::STAGE_U)
-      tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0 - G::UOX,
-                  y0 - G::UOY, 0, b);
+    tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0 - G::UOX,
+                y0 - G::UOY, 0, b);
   };
 
   if (tid == 0) {
@@ -1024,20 +1014,15 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
   for (int j = 0; j < nmine; ++j) {
     const int t = blockIdx.x + j * gridDim.x;
     const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
-    T *sphi = (T *)(smem + S * St::BYTES + (St::NSPHI == 2 ? (j & 1) : 0) * St::SPHI);
+    T *sphi = (T *)(smem + S * St::BYTES);
     const unsigned char *st = smem + (j % S) * St::BYTES;
     const Sm *shm = (const Sm *)st;
     const T *sh0 = (const T *)(st + St::HM);
     const T *spp = (const T *)(st + St::HM + St::H0);
     const Sm *sgm = (const Sm *)(st + St::HM + St::H0 + St::PP);
-    // u(t-1) of the own node: from the stage, or straight from global memory
-    // (the load is then in flight while the tile's phi is summed).
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < nx && gy < ny;
-    const size_t qn = (size_t)(active ? gy : 0) * nx + (active ? gx : 0);
     const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
-    const T upx = G::STAGE_U ? T(0) : a.u_in[qn];
-    const T upy = G::STAGE_U ? T(0) : a.u_in[a.V + qn];
     // 16-bit forms: u(t-1) and phi(t-1) of the node that slot k of node
     // (xn, yn) was streamed from; (cb, rb) is the node's position in the
     // u(t-1) and phi(t-1) boxes. Sources that wrap around the grid come from
@@ -1158,18 +1143,11 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
         phi_global<P, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
                           ly * SW + lx);
     }
-    // After this barrier every thread is done with tile j - 1. With one
-    // barrier per tile its stage is refilled here with tile j - 1 + S (sphi
-    // is double-buffered, so the stencils of tile j - 1 never race the phi
-    // of tile j); with two, at the end of the tile.
+    // phi of the tile and its ring complete (and the decision to stop
+    // CTA-wide).
     if (__syncthreads_or(!ok)) {
       failed_at = j;
       break;
-    }
-    if (!G::TWO_BARRIERS && tid == 0 && j > 0 && issued < nmine) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(issued);
-      ++issued;
     }
 
     if (active) {
@@ -1178,17 +1156,16 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
                                        0, 0, g, m);
       collide_stream<P, NP, false, WALL>(
           a, m, hreg, perr, g, pp,
-          G::STAGE_U ? sup[(ty + G::UOY) * G::UW + tx + G::UOX] : upx,
-          G::STAGE_U ? sup[(G::UH + ty + G::UOY) * G::UW + tx + G::UOX] : upy,
-          gx, gy);
+          sup[(ty + G::UOY) * G::UW + tx + G::UOX],
+          sup[(G::UH + ty + G::UOY) * G::UW + tx + G::UOX], gx, gy);
     }
-    if (G::TWO_BARRIERS) {
-      __syncthreads();
-      if (tid == 0 && issued < nmine) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(issued);
-        ++issued;
-      }
+    // Every thread is done with this tile's stage and phi tile: refill the
+    // stage with the tile S ahead.
+    __syncthreads();
+    if (tid == 0 && issued < nmine) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(issued);
+      ++issued;
     }
   }
   if (failed_at >= 0) {
