@@ -186,8 +186,9 @@ KArgs<P> make_args(const Consts &c, const Grid &g, int cur, int mode,
 
 template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
-// Moving population k (1..8) of phase i, or NS population k, at node q in
-// stored units: the value itself (FP64, FP32) or s f_k / w_k (16-bit forms).
+// Moving population k (1..8) of phase i, or NS population k, at node q as
+// stored: the value itself (FP64, FP32) or, 16-bit forms, s f_k / w_k less
+// the source-relative reference below (load_h_node, load_g_node add it).
 template <int P>
 __device__ __forceinline__ typename Prec<P>::T load_hm(const KArgs<P> &a, int i,
                                                        int k, size_t q) {
