@@ -231,6 +231,16 @@ lbm_status lbm_nphase_batch_step(lbm_nphase_batch_t *b, int64_t nsteps);
  * then returns LBM_ESTATE until the case is re-initialised). */
 lbm_nphase_t *lbm_nphase_batch_case(lbm_nphase_batch_t *b, int c);
 
+/* Macroscopic fields and diagnostics of case `c`: lbm_nphase_moments and
+ * lbm_nphase_diagnostics on its handle (same arguments, layout and errors;
+ * LBM_EINVAL for a case index outside 0..size-1). */
+lbm_status lbm_nphase_batch_moments(lbm_nphase_batch_t *b, int c, double *phi,
+                                    double *cfrac, double *u, double *p,
+                                    double *rho);
+lbm_status lbm_nphase_batch_diagnostics(lbm_nphase_batch_t *b, int c,
+                                        double *mass, double *ke,
+                                        double *umax);
+
 /* Time every kernel variant (generic at tile heights 4 and 8, and the
  * pipelined kernel when every case allows it) x schedule (strided, lists,
  * dynamic with chunks of 1, 4 and 16), with all resident CTAs, over

@@ -104,6 +104,8 @@ def load_library():
         lib.lbm_nphase_batch_step.argtypes = [vp, C.c_int64]
         lib.lbm_nphase_batch_case.argtypes = [vp, C.c_int]
         lib.lbm_nphase_batch_case.restype = vp
+        lib.lbm_nphase_batch_moments.argtypes = [vp, C.c_int, dp, dp, dp, dp, dp]
+        lib.lbm_nphase_batch_diagnostics.argtypes = [vp, C.c_int, dp, dp, dp]
         lib.lbm_nphase_batch_autotune.argtypes = [vp, C.c_int,
                                                   C.POINTER(C.c_double)]
         lib.lbm_nphase_batch_set_schedule.argtypes = [vp, C.POINTER(LbmSchedule)]
@@ -421,6 +423,23 @@ def lbm_nphase_batch_case(batch: int, case: int) -> int:
     return load_library().lbm_nphase_batch_case(C.c_void_p(batch), int(case))
 
 
+def lbm_nphase_batch_moments(batch: int, case: int, phi=None, c=None, u=None,
+                             p=None, rho=None):
+    _check(load_library().lbm_nphase_batch_moments(
+        C.c_void_p(batch), int(case), phi or None, c or None, u or None,
+        p or None, rho or None), "lbm_nphase_batch_moments")
+
+
+def lbm_nphase_batch_diagnostics(batch: int, case: int, N: int):
+    mass = np.zeros(N)
+    ke = np.zeros(1)
+    um = np.zeros(1)
+    _check(load_library().lbm_nphase_batch_diagnostics(
+        C.c_void_p(batch), int(case), mass.ctypes.data, ke.ctypes.data,
+        um.ctypes.data), "lbm_nphase_batch_diagnostics")
+    return mass, float(ke[0]), float(um[0])
+
+
 def lbm_nphase_batch_autotune(batch: int, trial_steps: int) -> float:
     ms = C.c_double()
     _check(load_library().lbm_nphase_batch_autotune(
@@ -524,11 +543,11 @@ class Batch:
                "u": t.empty((2,) + sh, dtype=t.float64, device=self.device),
                "p": t.empty(sh, dtype=t.float64, device=self.device),
                "rho": t.empty(sh, dtype=t.float64, device=self.device)}
-        lbm_nphase_moments(self.case_handle(case), out["phi"].data_ptr(),
-                           out["c"].data_ptr(), out["u"].data_ptr(),
-                           out["p"].data_ptr(), out["rho"].data_ptr())
+        lbm_nphase_batch_moments(self.handle, case, out["phi"].data_ptr(),
+                                 out["c"].data_ptr(), out["u"].data_ptr(),
+                                 out["p"].data_ptr(), out["rho"].data_ptr())
         return {k: v.cpu().numpy() for k, v in out.items()}
 
     def diagnostics(self, case: int):
-        return lbm_nphase_diagnostics(self.case_handle(case),
-                                      int(self.params[case]["N"]))
+        return lbm_nphase_batch_diagnostics(self.handle, case,
+                                            int(self.params[case]["N"]))

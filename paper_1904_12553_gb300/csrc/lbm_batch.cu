@@ -786,6 +786,20 @@ lbm_nphase_t *lbm_nphase_batch_case(lbm_nphase_batch_t *b, int c) {
   return b->cases[c];
 }
 
+lbm_status lbm_nphase_batch_moments(lbm_nphase_batch_t *b, int c, double *phi,
+                                    double *cfrac, double *u, double *p,
+                                    double *rho) {
+  if (!b || c < 0 || c >= b->n) return LBM_EINVAL;
+  return lbm_nphase_moments(b->cases[c], phi, cfrac, u, p, rho);
+}
+
+lbm_status lbm_nphase_batch_diagnostics(lbm_nphase_batch_t *b, int c,
+                                        double *mass, double *ke,
+                                        double *umax) {
+  if (!b || c < 0 || c >= b->n) return LBM_EINVAL;
+  return lbm_nphase_diagnostics(b->cases[c], mass, ke, umax);
+}
+
 lbm_status lbm_nphase_batch_set_schedule(lbm_nphase_batch_t *b,
                                          const lbm_nphase_batch_schedule *s) {
   if (!b || !s) return LBM_EINVAL;

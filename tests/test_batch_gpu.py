@@ -163,6 +163,30 @@ def test_autotune_and_reinit(cases, singles):
     b.close()
 
 
+def test_batch_moments_and_diagnostics_entry_points(cases):
+    """lbm_nphase_batch_moments / _diagnostics give what the single-grid
+    calls give on the case's handle, and reject a case index outside the
+    batch."""
+    from paper_1904_12553_gb300 import Batch, LbmError, binding
+    b = Batch([w.params for w in cases[:3]])
+    for i, w in enumerate(cases[:3]):
+        b.init(i, w.c0, w.u0)
+    b.step(5)
+    for i, w in enumerate(cases[:3]):
+        N = int(w.params["N"])
+        m1 = b.moments(i)
+        d1 = b.diagnostics(i)
+        d2 = binding.lbm_nphase_diagnostics(b.case_handle(i), N)
+        np.testing.assert_array_equal(d1[0], d2[0])
+        assert d1[1:] == d2[1:]
+        assert np.isfinite(m1["phi"]).all()
+    with pytest.raises(LbmError):
+        binding.lbm_nphase_batch_diagnostics(b.handle, 3, 3)
+    with pytest.raises(LbmError):
+        binding.lbm_nphase_batch_moments(b.handle, -1)
+    b.close()
+
+
 def test_batch_rejects_unsupported(cases):
     from paper_1904_12553_gb300 import binding
     p = dict(cases[0].params, precision="fp64")
