@@ -55,10 +55,11 @@ typedef enum {
 typedef enum {
   LBM_FP64 = 0,     /* FP64 storage and arithmetic */
   LBM_FP32 = 1,     /* FP32 storage and arithmetic */
-  LBM_MIX_BF16 = 2, /* moving populations stored as BF16 (f_k/w_k - 3 c_k.u f~) * s,
-                       f~ = phi_i (h) or N/Gamma (g), with u and phi_i of the
-                       node the population was streamed from (D2Q9; D3Q15:
-                       f_k/w_k * s); FP32 math */
+  LBM_MIX_BF16 = 2, /* moving populations stored as BF16 s (h_k/w_k - 3 c_k.u phi_i)
+                       and s (g_k/w_k - rho~ (3 c_k.u + 4.5 (c_k.u)^2 - 1.5
+                       |u|^2)), rho~ = N/Gamma, with u and phi_i of the node
+                       the population was streamed from (D2Q9; D3Q15:
+                       s f_k/w_k); FP32 math */
   LBM_MIX_FP16 = 3  /* the same with FP16 storage; FP32 math */
 } lbm_precision;
 

@@ -200,11 +200,12 @@ __device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
   return to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
 }
 
-// 16-bit forms: every moving population is stored relative to the advective
+// 16-bit forms: every moving population is stored relative to the velocity
 // part of its equilibrium (Eqs. 25, N25) evaluated at the node it was
 // streamed from: slot k of node y holds
-//     s f_k / w_k - 3 s (c_k . u) phi_i     (h of phase i)
-//     s g_k / w_k - 3 s (c_k . u) rho~      (g; rho~ = the constant N/Gamma)
+//     s h_k / w_k - 3 s (c_k . u) phi_i                          (h, phase i)
+//     s g_k / w_k - s rho~ (3 c_k.u + 4.5 (c_k.u)^2 - 1.5 |u|^2)  (g)
+// (rho~ = the constant N/Gamma)
 // with u = u(t), phi = phi(t) of the source node y - c_k (of y itself when
 // y - c_k lies behind a wall: the slot was filled by bounce-back). The writer
 // uses its own u(t), phi(t); the reader takes them as u(t-1), phi(t-1) of the
@@ -226,6 +227,17 @@ __device__ __forceinline__ float adv_units(float cu, float f, float s3) {
 }
 __device__ __forceinline__ double adv_units(double cu, double f, double s3) {
   return cu * f * s3;
+}
+// s rho~ (3 c_k.u + 4.5 (c_k.u)^2 - 1.5 |u|^2) in stored units; srho = s rho~.
+__device__ __forceinline__ float g_ref(float cu, float ux, float uy, float srho) {
+  const float uu = __fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy));
+  const float in = __fadd_rn(__fadd_rn(__fmul_rn(3.0f, cu), __fmul_rn(4.5f, __fmul_rn(cu, cu))),
+                             __fmul_rn(-1.5f, uu));
+  return __fmul_rn(in, srho);
+}
+__device__ __forceinline__ double g_ref(double cu, double ux, double uy,
+                                        double srho) {
+  return (3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy)) * srho;
 }
 
 // The node slot k of (x, y) was streamed from: (x, y) - c_k, periodic in x
@@ -271,8 +283,8 @@ __device__ __forceinline__ void load_g_node(const KArgs<P> &a, int x, int y,
     T v = load_gm<P>(a, k, q);
     if constexpr (Prec<P>::REF) {
       const size_t qs = source_node<WALL>(x, y, k, a.nx, a.ny);
-      const T cu = cdotu(k, ldg(a.u_in + qs), ldg(a.u_in + a.V + qs));
-      v = __fadd_rn(v, adv_units(cu, a.rho_base, T(3) * a.sg_st));
+      const T sux = ldg(a.u_in + qs), suy = ldg(a.u_in + a.V + qs);
+      v = __fadd_rn(v, g_ref(cdotu(k, sux, suy), sux, suy, a.rho_base * a.sg_st));
     }
     g[k] = v;
   }
@@ -589,7 +601,7 @@ __device__ __forceinline__ void collide_stream(
     if constexpr (Prec<P>::REF)
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] = to_S<typename Prec<P>::Sm>(
           keep_g * g[k] + a.sg_st * t -
-          adv_units(cdotu(kk, ux, uy), a.rho_base, T(3) * a.sg_st));
+          g_ref(cdotu(kk, ux, uy), ux, uy, a.rho_base * a.sg_st));
     else if constexpr (MIX)
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] =
           to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
@@ -1060,7 +1072,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
         for (int i = 0; i < NP; ++i) sph[i] = ldg(a.pp_in + (size_t)i * a.V + qs);
       }
     };
-    const T s3h = T(3) * a.sh_st, s3g = T(3) * a.sg_st;
+    const T s3h = T(3) * a.sh_st, srg = a.rho_base * a.sg_st;
     // A thread whose wait gave up still runs the phi sums below (on stale
     // shared data, harmlessly); the barrier after them makes the decision
     // to stop the same for the whole CTA.
@@ -1121,7 +1133,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
 #pragma unroll
           for (int i = 0; i < NP; ++i)
             hreg[i][k] = __fadd_rn(hreg[i][k], adv_units(cu, sph[i], s3h));
-          g[k] = __fadd_rn(g[k], adv_units(cu, a.rho_base, s3g));
+          g[k] = __fadd_rn(g[k], g_ref(cu, sux, suy, srg));
         }
       }
 #pragma unroll
@@ -1244,9 +1256,10 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
       const T geq = w_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
       if constexpr (Prec<P>::MIX) {
         const size_t qs = source_node<WALL>(x, y, k, nx, ny);
-        const T ref = Prec<P>::REF ? adv_units(cdotu(k, a.u_out[qs], a.u_out[V + qs]),
-                                               a.rho_base, T(3) * a.sg_st)
-                                   : T(0);
+        const T sux = a.u_out[qs], suy = a.u_out[V + qs];
+        const T ref = Prec<P>::REF
+                          ? g_ref(cdotu(k, sux, suy), sux, suy, a.rho_base * a.sg_st)
+                          : T(0);
         gm[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w_of<T>(k)) - ref);
       } else
         gm[(size_t)(k - 1) * V + q] = geq;
