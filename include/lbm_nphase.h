@@ -286,6 +286,16 @@ int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
  * kernels everywhere. All compute the same step. */
 int lbm_nphase_uses_pipelined_kernel(const lbm_nphase_t *h);
 
+/* Self-test of the timeout path (not part of the paper). Launches, on the
+ * handle's stream, one warp that waits with the library's bounded device
+ * wait (about a second) on a barrier nothing signals; when the wait gives up
+ * it sets the handle's device error word, exactly as a pipelined step kernel
+ * whose copies never arrived would. The next lbm_nphase_moments or
+ * lbm_nphase_diagnostics then returns LBM_ETIMEOUT and marks the handle, and
+ * lbm_nphase_step returns LBM_ESTATE until lbm_nphase_init. Asynchronous;
+ * faults nothing and leaves the context usable. */
+lbm_status lbm_nphase_selftest_wait_timeout(lbm_nphase_t *h);
+
 /* The last CUDA error code seen by the handle (0 if none). */
 int lbm_nphase_cuda_error(const lbm_nphase_t *h);
 

@@ -102,6 +102,7 @@ def load_library():
                                                 vp, C.POINTER(vp)]
         lib.lbm_nphase_batch_init.argtypes = [vp, C.c_int, dp, dp, C.c_double]
         lib.lbm_nphase_batch_step.argtypes = [vp, C.c_int64]
+        lib.lbm_nphase_selftest_wait_timeout.argtypes = [vp]
         lib.lbm_nphase_batch_case.argtypes = [vp, C.c_int]
         lib.lbm_nphase_batch_case.restype = vp
         lib.lbm_nphase_batch_moments.argtypes = [vp, C.c_int, dp, dp, dp, dp, dp]
@@ -417,6 +418,11 @@ def lbm_nphase_batch_step(batch: int, nsteps: int):
     _check(load_library().lbm_nphase_batch_step(C.c_void_p(batch),
                                                 int(nsteps)),
            "lbm_nphase_batch_step")
+
+
+def lbm_nphase_selftest_wait_timeout(handle: int):
+    _check(load_library().lbm_nphase_selftest_wait_timeout(C.c_void_p(handle)),
+           "lbm_nphase_selftest_wait_timeout")
 
 
 def lbm_nphase_batch_case(batch: int, case: int) -> int:

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm_nphase.so")
 SOURCES = ["lbm_capi.cu", "lbm_f64.cu", "lbm_f32.cu", "lbm_bf16.cu",
-           "lbm_f16.cu", "lbm_batch.cu"]
+           "lbm_f16.cu", "lbm_batch.cu", "lbm_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
