@@ -250,13 +250,14 @@ def e2e_run(w, prec, steps):
     return V * steps / t / 1e6, h2d / steps, d2h / steps
 
 
-def d3q15_run(n=256, steps=100):
+def d3q15_run(n=256, steps=100, prec="fp32"):
     """D3Q15 (three dimensions): three phases, two sphere drops R = n/6 in a
-    periodic n^3 box, FP32 storage, z-marching 3-D kernel."""
+    periodic n^3 box, z-marching 3-D kernel; FP32 storage, or 16-bit
+    storage relative to the velocity part of the equilibrium."""
     import torch
     from paper_1904_12553_gb300 import Solver, workloads as W
 
-    w = W.sphere_drops3(n=n, N=3, R=n / 6.0, precision="fp32")
+    w = W.sphere_drops3(n=n, N=3, R=n / 6.0, precision=prec)
     s = Solver(w.params)
     kernel = s.step_kernel
     s.init(w.c0)
@@ -272,9 +273,13 @@ def d3q15_run(n=256, steps=100):
     ms = e0.elapsed_time(e1) / steps
     s.close()
     N, V = 3, w.V
-    B = 2 * 4 * (15 * (N - 1) + 14 + (N - 1) + 3)
+    if prec == "fp32":
+        B = 2 * 4 * (15 * (N - 1) + 14 + (N - 1) + 3)
+    else:
+        # 14 moving h per phase and 14 g in 16 bits; d_0, phi(t-1), u(t-1)
+        B = 2 * (2 * (14 * (N - 1) + 14) + 4 * (2 * (N - 1) + 3))
     peak, _ = peaks()
-    return {"workload": f"N=3 two spheres, D3Q15 {n}^3 periodic, FP32",
+    return {"workload": f"N=3 two spheres, D3Q15 {n}^3 periodic, {prec.upper()}",
             "mlups": V / (ms / 1e3) / 1e6, "ms_per_step": ms,
             "alg_bytes_per_node": B,
             "hbm_frac": B * V / (ms / 1e3) / 1e9 / peak,
@@ -450,7 +455,8 @@ def run_ours(args, dist, rank, world):
                                  "2070 MHz)"}
     if not args.quick:
         forms["batch"] = batch_run()
-        forms["d3q15_fp32"] = d3q15_run()
+        for prec3 in ("fp32", "bf16", "fp16"):
+            forms["d3q15_" + prec3] = d3q15_run(prec=prec3)
     e2e_v, h2d, d2h = e2e_run(w, "fp32", args.steps)
     cpu = cpu_baseline() if (world == 1 and not args.quick) else None
     line = {
@@ -492,7 +498,8 @@ def run_only(args):
     if args.only == "batch":
         out = batch_run(steps=args.steps)
     elif args.only == "d3q15":
-        out = d3q15_run(n=args.n if args.n != 2048 else 128, steps=args.steps)
+        out = d3q15_run(n=args.n if args.n != 2048 else 128, steps=args.steps,
+                        prec=args.d3_prec)
     else:
         w = make_workload(args.only, n=args.n, accept=accept_sigma())
         ms, _, _, _, kernel = time_form(w, args.only, args.steps, args.warmup)
@@ -578,6 +585,8 @@ def main():
                     choices=["fp32", "bf16", "fp16", "fp64", "batch", "d3q15"],
                     help="time one form alone and print its line "
                          "(profiling captures)")
+    ap.add_argument("--d3-prec", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="storage form of --only d3q15")
     ap.add_argument("--n", type=int, default=2048,
                     help="grid side (2048 is the benchmark workload; smaller "
                          "sides are for profiling captures)")

@@ -78,31 +78,135 @@ __device__ __forceinline__ typename Prec<P>::T load_hm3(const KArgs<P> &a, int i
   return to_T(ldg(a.hm_in + ((size_t)(i * 14 + k - 1)) * a.V + q));
 }
 
-// phi_i at node q from the stored values (FP64: sum of the 15; other forms:
-// phi(t-1) + (d_0 + sum_k h_k), TwoSum error in err).
-template <int P>
-__device__ __forceinline__ typename Prec<P>::T node_phi3(const KArgs<P> &a, int i,
-                                                         size_t q,
-                                                         typename Prec<P>::T &err) {
+// 16-bit forms store every moving population relative to the velocity part
+// of its equilibrium at the node it was streamed from, as in two dimensions
+// (cdotu, adv_units, g_ref there): c_k . u with the same rounded operations
+// on writer and reader (D3Q15 has face and corner velocities only).
+__device__ __forceinline__ float cdotu3(int k, float ux, float uy, float uz) {
+  const int cx = c3x(k), cy = c3y(k), cz = c3z(k);
+  const float a = cx > 0 ? ux : -ux, b = cy > 0 ? uy : -uy, c = cz > 0 ? uz : -uz;
+  if (cx != 0 && cy != 0 && cz != 0) return __fadd_rn(__fadd_rn(a, b), c);
+  return cx != 0 ? a : (cy != 0 ? b : c);
+}
+__device__ __forceinline__ double cdotu3(int k, double ux, double uy, double uz) {
+  return c3x(k) * ux + c3y(k) * uy + c3z(k) * uz;
+}
+__device__ __forceinline__ float g_ref3(float cu, float ux, float uy, float uz,
+                                        float srho) {
+  const float uu = __fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)),
+                             __fmul_rn(uz, uz));
+  const float in = __fadd_rn(__fadd_rn(__fmul_rn(3.0f, cu), __fmul_rn(4.5f, __fmul_rn(cu, cu))),
+                             __fmul_rn(-1.5f, uu));
+  return __fmul_rn(in, srho);
+}
+__device__ __forceinline__ double g_ref3(double cu, double ux, double uy,
+                                         double uz, double srho) {
+  return (3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy + uz * uz)) * srho;
+}
+// The node slot k of (x, y, z) was streamed from: (x, y, z) - c_k, periodic
+// in x and z (and y without walls); behind a wall, (x, y, z) itself.
+template <bool WALL>
+__device__ __forceinline__ size_t source3(int x, int y, int z, int k, int nx,
+                                          int ny, int nz) {
+  int sx = x - c3x(k), sy = y - c3y(k), sz = z - c3z(k);
+  if (WALL && (sy < 0 || sy >= ny)) {
+    sx = x;
+    sy = y;
+    sz = z;
+  }
+  sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+  sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+  sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+  return ((size_t)sz * ny + sy) * nx + sx;
+}
+// The sources of one node's 14 moving slots, (x, y, z) - c_k, from wrapped
+// x - 1..x + 1 and the row and plane offsets of y - 1..y + 1, z - 1..z + 1
+// (computed once per node instead of once per slot); behind a wall in y the
+// node itself. The same indices as source3.
+template <bool WALL> struct Nb3 {
+  size_t q, pz[3], ry[3];
+  int xv[3];
+  bool lo, hi;
+  __device__ __forceinline__ Nb3(int x, int y, int z, size_t q_, int nx, int ny,
+                                 int nz) {
+    q = q_;
+    xv[0] = x == 0 ? nx - 1 : x - 1;
+    xv[1] = x;
+    xv[2] = x + 1 >= nx ? x + 1 - nx : x + 1;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      int yy = y + j - 1, zz = z + j - 1;
+      if (WALL)
+        yy = yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy);
+      else
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+      zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+      ry[j] = (size_t)yy * nx;
+      pz[j] = (size_t)zz * ny * nx;
+    }
+    lo = WALL && y == 0;
+    hi = WALL && y == ny - 1;
+  }
+  __device__ __forceinline__ size_t src(int k) const {
+    const int cx = c3x(k), cy = c3y(k), cz = c3z(k);
+    if (WALL && ((cy > 0 && lo) || (cy < 0 && hi))) return q;
+    return pz[1 - cz] + ry[1 - cy] + (size_t)xv[1 - cx];
+  }
+};
+
+// phi_i of every phase at node (x, y, z) = q from the stored values (FP64:
+// sum of the 15; other forms: phi(t-1) + (d_0 + sum_k h_k), TwoSum error
+// dropped). 16-bit forms decode slot k with u(t-1), phi(t-1) of its source,
+// looked up once for all phases. With OWN, the node's decoded h^i_1..14 and
+// g_1..14 also go to own[slot * stride] (slot i * 14 + k - 1, then
+// (NP - 1) * 14 + 13 + k for g), for the node's own step to read back.
+template <int P, int NP, bool WALL, bool OWN = false>
+__device__ __forceinline__ void node_phis3(const KArgs<P> &a, int nz, int x,
+                                           int y, int z, size_t q,
+                                           typename Prec<P>::T (&phi)[NP],
+                                           typename Prec<P>::T *own = nullptr,
+                                           int stride = 0) {
   typedef typename Prec<P>::T T;
-  T small = ldg(a.h0_in + (size_t)i * a.V + q);
+  const size_t V = a.V;
+  T small[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) small[i] = ldg(a.h0_in + (size_t)i * V + q);
+  const Nb3<WALL> nb(x, y, z, q, a.nx, a.ny, nz);
 #pragma unroll
   for (int k = 1; k < 15; ++k) {
-    const T x = load_hm3<P>(a, i, k, q);
-    if constexpr (Prec<P>::MIX)
-      small = __fmaf_rn(w3_of<T>(k) * a.sh_ld, x, small);
-    else
-      small = __fadd_rn_T(small, x);
+    T cu = T(0), ux = T(0), uy = T(0), uz = T(0);
+    size_t qs = q;
+    if constexpr (Prec<P>::REF) {
+      qs = nb.src(k);
+      ux = ldg(a.u_in + qs);
+      uy = ldg(a.u_in + V + qs);
+      uz = ldg(a.u_in + 2 * V + qs);
+      cu = cdotu3(k, ux, uy, uz);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T x_ = load_hm3<P>(a, i, k, q);
+      if constexpr (Prec<P>::REF)
+        x_ = __fadd_rn(x_, adv_units(cu, ldg(a.pp_in + (size_t)i * V + qs), T(3) * a.sh_st));
+      if constexpr (OWN) own[(i * 14 + k - 1) * stride] = x_;
+      if constexpr (Prec<P>::MIX)
+        small[i] = __fmaf_rn(w3_of<T>(k) * a.sh_ld, x_, small[i]);
+      else
+        small[i] = __fadd_rn_T(small[i], x_);
+    }
+    if constexpr (OWN) {
+      T gk = to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q));
+      if constexpr (Prec<P>::REF)
+        gk = __fadd_rn(gk, g_ref3(cu, ux, uy, uz, a.rho_base * a.sg_st));
+      own[(NP * 14 + k - 1) * stride] = gk;
+    }
   }
-  if constexpr (P == LBM_FP64) {
-    err = T(0);
-    return small;
-  } else {
-    const T pp = ldg(a.pp_in + (size_t)i * a.V + q);
-    const T s = __fadd_rn(pp, small);
-    const T bb = __fsub_rn(s, pp);
-    err = __fadd_rn(__fsub_rn(pp, __fsub_rn(s, bb)), __fsub_rn(small, bb));
-    return s;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    if constexpr (P == LBM_FP64)
+      phi[i] = small[i];
+    else
+      phi[i] = __fadd_rn(ldg(a.pp_in + (size_t)i * V + q), small[i]);
   }
 }
 
@@ -120,9 +224,11 @@ template <int P, int NP> struct Own3 {
   T h[NP][15], g[15], pp[NP], up[3];
 };
 
-template <int P, int NP>
-__device__ __forceinline__ void load_own3(const KArgs<P> &a, size_t q,
+template <int P, int NP, bool WALL>
+__device__ __forceinline__ void load_own3(const KArgs<P> &a, int nz, int x,
+                                          int y, int z, size_t q,
                                           Own3<P, NP> &o) {
+  typedef typename Prec<P>::T T;
   const size_t V = a.V;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
@@ -133,11 +239,45 @@ __device__ __forceinline__ void load_own3(const KArgs<P> &a, size_t q,
   }
 #pragma unroll
   for (int k = 1; k < 15; ++k) o.g[k] = to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q));
+  if constexpr (Prec<P>::REF) {
+    const Nb3<WALL> nb(x, y, z, q, a.nx, a.ny, nz);
+#pragma unroll
+    for (int k = 1; k < 15; ++k) {
+      const size_t qs = nb.src(k);
+      const T ux = ldg(a.u_in + qs), uy = ldg(a.u_in + V + qs),
+              uz = ldg(a.u_in + 2 * V + qs);
+      const T cu = cdotu3(k, ux, uy, uz);
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+        o.h[i][k] = __fadd_rn(o.h[i][k], adv_units(cu, ldg(a.pp_in + (size_t)i * V + qs),
+                                                   T(3) * a.sh_st));
+      o.g[k] = __fadd_rn(o.g[k], g_ref3(cu, ux, uy, uz, a.rho_base * a.sg_st));
+    }
+  }
 #pragma unroll
   for (int d = 0; d < 3; ++d) o.up[d] = a.u_in[(size_t)d * V + q];
 }
 
-// phi_i from a node's values in registers, summed in the order of node_phi3.
+// The same values, h and g decoded by node_phis3<..., OWN> into own[].
+template <int P, int NP>
+__device__ __forceinline__ void load_own3c(const KArgs<P> &a, size_t q,
+                                           const typename Prec<P>::T *own,
+                                           int stride, Own3<P, NP> &o) {
+  const size_t V = a.V;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    o.h[i][0] = ldg(a.h0_in + (size_t)i * V + q);
+#pragma unroll
+    for (int k = 1; k < 15; ++k) o.h[i][k] = own[(i * 14 + k - 1) * stride];
+    o.pp[i] = ldg(a.pp_in + (size_t)i * V + q);
+  }
+#pragma unroll
+  for (int k = 1; k < 15; ++k) o.g[k] = own[(NP * 14 + k - 1) * stride];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) o.up[d] = a.u_in[(size_t)d * V + q];
+}
+
+// phi_i from a node's values in registers, summed in the order of node_phis3.
 template <int P>
 __device__ __forceinline__ typename Prec<P>::T node_phi3r(
     const typename Prec<P>::T *h, typename Prec<P>::T pp,
@@ -245,8 +385,11 @@ __device__ __forceinline__ void collide3(
                E2 * (cx * J[0] + cy * J[1] + cz * J[2]);
     const T t = A0 + C1 * cF + cu * inner;
     if constexpr (MIX)
-      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] =
-          to_S<typename Prec<P>::Sm>(keep_g * o.g[k] + a.sg_st * t);
+      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = to_S<typename Prec<P>::Sm>(
+          keep_g * o.g[k] + a.sg_st * t -
+          (Prec<P>::REF ? g_ref3(cdotu3(dk[k], u[0], u[1], u[2]), u[0], u[1], u[2],
+                                 a.rho_base * a.sg_st)
+                        : T(0)));
     else
       a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = keep_g * o.g[k] + w3_of<T>(k) * t;
   }
@@ -273,9 +416,14 @@ __device__ __forceinline__ void collide3(
       const T hk = o.h[i][k];
       const size_t oo = ((size_t)(i * 14 + dk[k] - 1)) * V + dst[k];
       if constexpr (MIX) {
-        const auto sv = to_S<typename Prec<P>::Sm>(keep * hk + t);
+        // relative to the velocity part at this node, the slot's source
+        const T ref = Prec<P>::REF
+                          ? adv_units(cdotu3(dk[k], u[0], u[1], u[2]), ph[i], T(3) * a.sh_st)
+                          : T(0);
+        const auto sv = to_S<typename Prec<P>::Sm>(keep * hk + t - ref);
         a.hm_out[oo] = sv;
-        moving_sum = __fmaf_rn(w3_of<T>(k) * a.sh_ld, to_T(sv), moving_sum);
+        moving_sum = __fmaf_rn(w3_of<T>(k) * a.sh_ld, __fadd_rn(to_T(sv), ref),
+                               moving_sum);
       } else {
         const T hs = keep * hk + w3_of<T>(k) * t;
         a.hm_out[oo] = hs;
@@ -322,12 +470,13 @@ __global__ void __launch_bounds__(NT3, P == LBM_FP64 ? 1 : 2)
   // 1. phi on the box (tile + halo R), wrapped / ghost coordinates.
   for (int r = tid; r < PL; r += NT3) {
     const int lx = r % W, ly = (r / W) % H, lz = r / (W * H);
-    const size_t q = node3<WALL>(x0 - R + lx, y0 - R + ly, z0 - R + lz, nx, ny, nz);
+    const int hx = wrap(x0 - R + lx, nx), hy = wrap_y<WALL>(y0 - R + ly, ny),
+              hz = wrap(z0 - R + lz, nz);
+    const size_t q = ((size_t)hz * ny + hy) * nx + hx;
+    T phv[NP];
+    node_phis3<P, NP, WALL>(a, nz, hx, hy, hz, q, phv);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      T e;
-      sphi[i * PL + r] = node_phi3<P>(a, i, q, e);
-    }
+    for (int i = 0; i < NP; ++i) sphi[i * PL + r] = phv[i];
   }
   __syncthreads();
   // 2. Unequal densities: C on the tile and a ring of radius 1; wall ghost
@@ -404,7 +553,8 @@ __global__ void __launch_bounds__(NT3, P == LBM_FP64 ? 1 : 2)
   }
   // own-node values (node 0 stands in for inactive threads)
   Own3<P, NP> own;
-  load_own3<P, NP>(a, q, own);
+  load_own3<P, NP, WALL>(a, nz, active ? gx : 0, active ? gy : 0, active ? gz : 0,
+                         q, own);
   T F[3], u[3], uu, pr;
   macros3<P, NP>(a, gp, Cv, rho, gr, own.g, u, F, uu, pr);
   if (a.mode == MODE_MOMENTS) {
@@ -457,6 +607,11 @@ __global__ void __launch_bounds__(NT3, P == LBM_FP64 ? 1 : 2)
 // one of tile3_kernel (macros3, collide3).
 // ---------------------------------------------------------------------------
 constexpr int MX3 = 32, MY3 = 8, MT3 = MX3 * MY3;
+// dynamic shared memory of march3_kernel: 14 (N - 1) + 14 decoded values
+// per column
+template <int P, int NP> constexpr size_t march3_smem() {
+  return (size_t)(NP * 14 + 14) * MT3 * sizeof(typename Prec<P>::T);
+}
 
 // Eq. N31 on D3Q15 from three planes (z - 1, z, z + 1) of stride W, pairs of
 // opposite velocities summed in the order of stencil3.
@@ -492,6 +647,9 @@ __global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
   const KArgs<P> &a = A.a;
   constexpr int SW = MX3 + 2, SH = MY3 + 2, PL = SW * SH;
   __shared__ T win[3][NP][PL];
+  // the own column's decoded h and g of the plane summed last (march3_smem)
+  extern __shared__ __align__(16) unsigned char smem_m3[];
+  T *ocache = (T *)smem_m3;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MX3 + tx;
   const int nx = a.nx, ny = a.ny, nz = A.nz;
   const int x0 = blockIdx.x * MX3, y0 = blockIdx.y * MY3;
@@ -507,34 +665,34 @@ __global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
     T(*w)[PL] = win[slot(z)];
     const int zz = wrap(z, nz);
     {
-      const size_t q = ((size_t)zz * ny + wrap_y<WALL>(gy, ny)) * nx + wrap(gx, nx);
+      const int cx = wrap(gx, nx), cy = wrap_y<WALL>(gy, ny);
+      const size_t q = ((size_t)zz * ny + cy) * nx + cx;
+      T phv[NP];
+      node_phis3<P, NP, WALL, true>(a, nz, cx, cy, zz, q, phv, ocache + tid, MT3);
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T e;
-        w[i][(ty + 1) * SW + tx + 1] = node_phi3<P>(a, i, q, e);
-      }
+      for (int i = 0; i < NP; ++i) w[i][(ty + 1) * SW + tx + 1] = phv[i];
     }
     constexpr int NRING = PL - MT3;
     static_assert(NRING <= MT3, "one ring position per thread");
     if (tid < NRING) {
       int lx, ly;
       ring_pos_1<MY3>(tid, lx, ly);
-      const size_t q = node3<WALL>(x0 - 1 + lx, y0 - 1 + ly, zz, nx, ny, nz);
+      const int rx = wrap(x0 - 1 + lx, nx), ry = wrap_y<WALL>(y0 - 1 + ly, ny);
+      const size_t q = ((size_t)zz * ny + ry) * nx + rx;
+      T phv[NP];
+      node_phis3<P, NP, WALL>(a, nz, rx, ry, zz, q, phv);
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T e;
-        w[i][ly * SW + lx] = node_phi3<P>(a, i, q, e);
-      }
+      for (int i = 0; i < NP; ++i) w[i][ly * SW + lx] = phv[i];
     }
   };
   plane_phi(zs - 1);
   plane_phi(zs);
   for (int z = zs; z < ze; ++z) {
-    // this plane's own-node loads first, in flight while phi of the next
-    // plane is summed
+    // this plane's own-node values (decoded when phi of this plane was
+    // summed) first, then phi of the next plane
     const size_t q = col ? ((size_t)z * ny + gy) * nx + gx : 0;
     Own3<P, NP> own;
-    load_own3<P, NP>(a, q, own);
+    load_own3c<P, NP>(a, q, ocache + tid, MT3, own);
     plane_phi(z + 1);
     __syncthreads();
     if (col) {
@@ -617,9 +775,15 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
     for (int k = 1; k < 15; ++k) {
       const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
       const T geq = w3_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-      if constexpr (Prec<P>::MIX)
-        a.gm_out[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w3_of<T>(k)));
-      else
+      if constexpr (Prec<P>::MIX) {
+        const size_t qs = source3<WALL>(x, y, z, k, nx, ny, nz);
+        const T sux = a.u_out[qs], suy = a.u_out[V + qs], suz = a.u_out[2 * V + qs];
+        a.gm_out[(size_t)(k - 1) * V + q] = to_S<Sm>(
+            geq * (a.sg_st / w3_of<T>(k)) -
+            (Prec<P>::REF ? g_ref3(cdotu3(k, sux, suy, suz), sux, suy, suz,
+                                   a.rho_base * a.sg_st)
+                          : T(0)));
+      } else
         a.gm_out[(size_t)(k - 1) * V + q] = geq;
     }
     for (int i = 0; i < NP; ++i) {
@@ -631,9 +795,15 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
         const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
         const T heq = w3_of<T>(k) * (aC + T(3) * ph[i] * cu);
         if constexpr (Prec<P>::MIX) {
-          const Sm sv = to_S<Sm>(heq * (a.sh_st / w3_of<T>(k)));
+          const size_t qs = source3<WALL>(x, y, z, k, nx, ny, nz);
+          const T ref =
+              Prec<P>::REF
+                  ? adv_units(cdotu3(k, a.u_out[qs], a.u_out[V + qs], a.u_out[2 * V + qs]),
+                              a.pp_out[(size_t)i * V + qs], T(3) * a.sh_st)
+                  : T(0);
+          const Sm sv = to_S<Sm>(heq * (a.sh_st / w3_of<T>(k)) - ref);
           a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = sv;
-          moving = __fmaf_rn(w3_of<T>(k) * a.sh_ld, to_T(sv), moving);
+          moving = __fmaf_rn(w3_of<T>(k) * a.sh_ld, __fadd_rn(to_T(sv), ref), moving);
         } else {
           a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = heq;
           moving = __fadd_rn_T(moving, heq);
@@ -664,7 +834,16 @@ cudaError_t launch_tile3_t(const Consts &c, const Grid &g, int cur, int mode,
       if (zl > g.nz) zl = g.nz;
       const int zlen = (int)zl;
       dim3 grid(tiles_x(g.nx), (g.ny + MY3 - 1) / MY3, (g.nz + zlen - 1) / zlen);
-      march3_kernel<P, NP, WALL><<<grid, dim3(MX3, MY3), 0, s>>>(A, zlen);
+      constexpr size_t msm = march3_smem<P, NP>();
+      static bool mattr = false;
+      if (!mattr) {
+        cudaError_t e = cudaFuncSetAttribute(march3_kernel<P, NP, WALL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)msm);
+        if (e != cudaSuccess) return e;
+        mattr = true;
+      }
+      march3_kernel<P, NP, WALL><<<grid, dim3(MX3, MY3), msm, s>>>(A, zlen);
       return cudaGetLastError();
     }
   }
