@@ -608,9 +608,13 @@ __global__ void __launch_bounds__(NT3, P == LBM_FP64 ? 1 : 2)
 // ---------------------------------------------------------------------------
 constexpr int MX3 = 32, MY3 = 8, MT3 = MX3 * MY3;
 // dynamic shared memory of march3_kernel: 14 (N - 1) + 14 decoded values
-// per column
-template <int P, int NP> constexpr size_t march3_smem() {
+// per column, then the three-plane phi window (tile and xy ring)
+template <int P, int NP> __host__ __device__ constexpr size_t march3_cache_bytes() {
   return (size_t)(NP * 14 + 14) * MT3 * sizeof(typename Prec<P>::T);
+}
+template <int P, int NP> __host__ __device__ constexpr size_t march3_smem() {
+  return march3_cache_bytes<P, NP>() +
+         (size_t)3 * NP * (MX3 + 2) * (MY3 + 2) * sizeof(typename Prec<P>::T);
 }
 
 // Eq. N31 on D3Q15 from three planes (z - 1, z, z + 1) of stride W, pairs of
@@ -646,10 +650,11 @@ __global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
   typedef typename Prec<P>::T T;
   const KArgs<P> &a = A.a;
   constexpr int SW = MX3 + 2, SH = MY3 + 2, PL = SW * SH;
-  __shared__ T win[3][NP][PL];
-  // the own column's decoded h and g of the plane summed last (march3_smem)
+  // the own column's decoded h and g of the plane summed last, then the
+  // window (march3_smem)
   extern __shared__ __align__(16) unsigned char smem_m3[];
   T *ocache = (T *)smem_m3;
+  T(*win)[NP][PL] = (T(*)[NP][PL])(smem_m3 + march3_cache_bytes<P, NP>());
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MX3 + tx;
   const int nx = a.nx, ny = a.ny, nz = A.nz;
   const int x0 = blockIdx.x * MX3, y0 = blockIdx.y * MY3;
@@ -661,6 +666,9 @@ __global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
   auto slot = [&](int z) { return (z - zs + 1) % 3; };
   // phi of plane z on the tile (wrapped where the tile overhangs the grid)
   // and its xy ring
+  // (the own column's decoded values go to the cache, also on the two
+  // planes outside the slab, where they are not used: a guard there cost
+  // the 16-bit forms 40%)
   auto plane_phi = [&](int z) {
     T(*w)[PL] = win[slot(z)];
     const int zz = wrap(z, nz);
