@@ -147,12 +147,15 @@ def test_d3q15_fp16_resting_spheres_2e4_steps():
     assert md(g["phi"], ref["phi"]) <= 1e-3
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_d3q15_quiescent_exact(prec):
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("rho", [[2, 1, 3, 7], None])
+def test_d3q15_quiescent_exact(prec, rho):
+    """A uniform mixture at rest stays exactly at rest in every storage form,
+    on the 3-D tile kernel (unequal densities) and the z-marching one."""
     N, sh = 4, (6, 9, 40)
     c = np.broadcast_to(np.array([0.1, 0.2, 0.3, 0.4])[:, None, None, None],
                         (N,) + sh).copy()
-    p = W.base_params3(N, sh[2], sh[1], sh[0], 1e-3, rho=[2, 1, 3, 7],
+    p = W.base_params3(N, sh[2], sh[1], sh[0], 1e-3, rho=rho,
                        precision=prec, wall_y=1)
     w = W.Workload("q3", p, c)
     g = gpu3(w, 300)

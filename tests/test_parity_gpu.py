@@ -337,10 +337,15 @@ def test_pipelined_kernel_matches_generic(N, prec, nx, ny, wall):
 # Properties and API behaviour
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("wall", [0, 1])
-def test_quiescent_exact(prec, wall):
-    w = W.quiescent(4, 40, 19, frac=[0.1, 0.2, 0.3, 0.4], rho=[2, 1, 3, 7],
+@pytest.mark.parametrize("rho", [[2, 1, 3, 7], None])
+def test_quiescent_exact(prec, wall, rho):
+    """A uniform mixture at rest stays exactly at rest, in every storage
+    form, on the generic kernel (unequal densities) and the pipelined one
+    (equal densities): every node computes the same numbers and opposite
+    populations stay equal."""
+    w = W.quiescent(4, 40, 19, frac=[0.1, 0.2, 0.3, 0.4], rho=rho,
                     precision=prec, wall_y=wall)
     g = gpu_run(w, 500)
     assert np.abs(g["u"]).max() == 0.0
