@@ -479,6 +479,8 @@ def run_ours(args, dist, rank, world):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "segments": segment_summary(segs, V),
+        # the same rate counted per LB equation (N per node update)
+        "equation_mlups": value * N,
         "clocks": clocks,
         "forms": forms,
         "check": {"mass": list(map(float, mass)), "ke": float(ke)},
