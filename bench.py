@@ -39,9 +39,11 @@ def alg_bytes_per_node(N: int, prec: str) -> int:
     """Algorithmic bytes per node-step: read + write of 9(N-1) h + 8 g +
     (N-1) phi_prev + 2 u_prev; the 8N moving populations in the storage
     type, the N-1 rest slots and the N+1 state values in the arithmetic
-    type."""
+    type. The 16-bit forms also carry p(t-1), which their g storage is
+    relative to."""
     s_mov, s_rest = BYTES_PER_VALUE[prec]
-    return 2 * (8 * N * s_mov + (N - 1) * s_rest + (N + 1) * s_rest)
+    extra = 1 if s_mov == 2 else 0
+    return 2 * (8 * N * s_mov + (N - 1) * s_rest + (N + 1 + extra) * s_rest)
 
 
 # FP64 operations one node-step executes in the FP64 form at N=5 (ncu
@@ -276,8 +278,9 @@ def d3q15_run(n=256, steps=100, prec="fp32"):
     if prec == "fp32":
         B = 2 * 4 * (15 * (N - 1) + 14 + (N - 1) + 3)
     else:
-        # 14 moving h per phase and 14 g in 16 bits; d_0, phi(t-1), u(t-1)
-        B = 2 * (2 * (14 * (N - 1) + 14) + 4 * (2 * (N - 1) + 3))
+        # 14 moving h per phase and 14 g in 16 bits; d_0, phi(t-1), u(t-1),
+        # p(t-1)
+        B = 2 * (2 * (14 * (N - 1) + 14) + 4 * (2 * (N - 1) + 4))
     peak, _ = peaks()
     return {"workload": f"N=3 two spheres, D3Q15 {n}^3 periodic, {prec.upper()}",
             "mlups": V / (ms / 1e3) / 1e6, "ms_per_step": ms,

@@ -56,10 +56,10 @@ typedef enum {
   LBM_FP64 = 0,     /* FP64 storage and arithmetic */
   LBM_FP32 = 1,     /* FP32 storage and arithmetic */
   LBM_MIX_BF16 = 2, /* moving populations stored as BF16 s (h_k/w_k - 3 c_k.u phi_i)
-                       and s (g_k/w_k - rho~ (3 c_k.u + 4.5 (c_k.u)^2 - 1.5
-                       |u|^2)), rho~ = N/Gamma, with u and phi_i of the node
-                       the population was streamed from (D2Q9 and D3Q15);
-                       FP32 math */
+                       and s (g_k/w_k - 3 p - rho~ (3 c_k.u + 4.5 (c_k.u)^2
+                       - 1.5 |u|^2)), rho~ = N/Gamma, with u, p and phi_i at
+                       t - 1 of the node the population was streamed from
+                       (D2Q9 and D3Q15); FP32 math */
   LBM_MIX_FP16 = 3  /* the same with FP16 storage; FP32 math */
 } lbm_precision;
 

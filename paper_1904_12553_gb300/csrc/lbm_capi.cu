@@ -176,10 +176,15 @@ struct Layout {
 int moving_dirs(const lbm_nphase_params *p) { return p->lattice == 1 ? 14 : 8; }
 int dims(const lbm_nphase_params *p) { return p->lattice == 1 ? 3 : 2; }
 int depth(const lbm_nphase_params *p) { return p->lattice == 1 ? p->nz : 1; }
+// Planes of the u(t-1) buffers: the D velocity components, and for the
+// 16-bit forms p(t-1), which their g storage is relative to.
+int uplanes(const lbm_nphase_params *p) {
+  return dims(p) + (p->precision == LBM_MIX_BF16 || p->precision == LBM_MIX_FP16 ? 1 : 0);
+}
 
 Layout layout(const lbm_nphase_params *p) {
   const size_t V = (size_t)p->nx * p->ny * depth(p);
-  const int NP = p->N - 1, QM = moving_dirs(p), D = dims(p);
+  const int NP = p->N - 1, QM = moving_dirs(p), D = dims(p), UP = uplanes(p);
   const size_t sT = p->precision == LBM_FP64 ? 8 : 4;
   const size_t sS = p->precision == LBM_FP64 ? 8 : (p->precision == LBM_FP32 ? 4 : 2);
   const size_t tiles = lbm::tiles_total(p->lattice, p->nx, p->ny, depth(p));
@@ -189,7 +194,7 @@ Layout layout(const lbm_nphase_params *p) {
   L.hm = off;       off += 2 * align256(NP * QM * V * sS);
   L.gm = off;       off += 2 * align256(QM * V * sS);
   L.phi_prev = off; off += 2 * align256(NP * V * sT);
-  L.u_prev = off;   off += 2 * align256(D * V * sT);
+  L.u_prev = off;   off += 2 * align256(UP * V * sT);
   L.stage = off;    off += align256((p->N + D) * V * 8);
   L.red = off;      off += align256(tiles * (p->N + 2) * 8);
   L.red_out = off;  off += align256(8 * 8);
@@ -487,7 +492,7 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   const size_t ppb = align256(n * g.V * sT);
   g.phi_prev[0] = base + L.phi_prev;
   g.phi_prev[1] = base + L.phi_prev + ppb;
-  const size_t upb = align256((size_t)dims(p) * g.V * sT);
+  const size_t upb = align256((size_t)uplanes(p) * g.V * sT);
   g.u_prev[0] = base + L.u_prev;
   g.u_prev[1] = base + L.u_prev + upb;
   h->stage = (double *)(base + L.stage);
@@ -631,12 +636,12 @@ int state_parts(const lbm_nphase_t *h, Part out[5]) {
   const size_t sT = h->prec == LBM_FP64 ? 8 : 4;
   const size_t sS = h->prec == LBM_FP64 ? 8 : (h->prec == LBM_FP32 ? 4 : 2);
   const int c = h->cur;
-  const int QM = moving_dirs(&h->prm), D = dims(&h->prm);
+  const int QM = moving_dirs(&h->prm), UP = uplanes(&h->prm);
   out[0] = {h->g.h0[c], n * V * sT};
   out[1] = {h->g.hm[c], n * QM * V * sS};
   out[2] = {h->g.gm[c], QM * V * sS};
   out[3] = {h->g.phi_prev[c], n * V * sT};
-  out[4] = {h->g.u_prev[c], D * V * sT};
+  out[4] = {h->g.u_prev[c], UP * V * sT};
   return 5;
 }
 }  // namespace

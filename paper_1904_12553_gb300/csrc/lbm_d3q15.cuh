@@ -103,6 +103,12 @@ __device__ __forceinline__ double g_ref3(double cu, double ux, double uy,
                                          double uz, double srho) {
   return (3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy + uz * uz)) * srho;
 }
+// The same plus the pressure part 3 s p (s3 = 3 s); p(t-1) is the fourth
+// plane of the u(t-1) buffers of the 16-bit forms.
+template <typename T>
+__device__ __forceinline__ T g_ref3p(T cu, T ux, T uy, T uz, T p, T srho, T s3) {
+  return __fadd_rn(g_ref3(cu, ux, uy, uz, srho), __fmul_rn(p, s3));
+}
 // The node slot k of (x, y, z) was streamed from: (x, y, z) - c_k, periodic
 // in x and z (and y without walls); behind a wall, (x, y, z) itself.
 template <bool WALL>
@@ -197,7 +203,8 @@ __device__ __forceinline__ void node_phis3(const KArgs<P> &a, int nz, int x,
     if constexpr (OWN) {
       T gk = to_T(ldg(a.gm_in + (size_t)(k - 1) * V + q));
       if constexpr (Prec<P>::REF)
-        gk = __fadd_rn(gk, g_ref3(cu, ux, uy, uz, a.rho_base * a.sg_st));
+        gk = __fadd_rn(gk, g_ref3p(cu, ux, uy, uz, ldg(a.u_in + 3 * V + qs),
+                                   a.rho_base * a.sg_st, T(3) * a.sg_st));
       own[(NP * 14 + k - 1) * stride] = gk;
     }
   }
@@ -251,7 +258,8 @@ __device__ __forceinline__ void load_own3(const KArgs<P> &a, int nz, int x,
       for (int i = 0; i < NP; ++i)
         o.h[i][k] = __fadd_rn(o.h[i][k], adv_units(cu, ldg(a.pp_in + (size_t)i * V + qs),
                                                    T(3) * a.sh_st));
-      o.g[k] = __fadd_rn(o.g[k], g_ref3(cu, ux, uy, uz, a.rho_base * a.sg_st));
+      o.g[k] = __fadd_rn(o.g[k], g_ref3p(cu, ux, uy, uz, ldg(a.u_in + 3 * V + qs),
+                                         a.rho_base * a.sg_st, T(3) * a.sg_st));
     }
   }
 #pragma unroll
@@ -387,8 +395,8 @@ __device__ __forceinline__ void collide3(
     if constexpr (MIX)
       a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = to_S<typename Prec<P>::Sm>(
           keep_g * o.g[k] + a.sg_st * t -
-          (Prec<P>::REF ? g_ref3(cdotu3(dk[k], u[0], u[1], u[2]), u[0], u[1], u[2],
-                                 a.rho_base * a.sg_st)
+          (Prec<P>::REF ? g_ref3p(cdotu3(dk[k], u[0], u[1], u[2]), u[0], u[1], u[2], pr,
+                                  a.rho_base * a.sg_st, T(3) * a.sg_st)
                         : T(0)));
     else
       a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = keep_g * o.g[k] + w3_of<T>(k) * t;
@@ -441,6 +449,7 @@ __device__ __forceinline__ void collide3(
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) a.u_out[(size_t)d * V + q] = u[d];
+  if constexpr (Prec<P>::REF) a.u_out[3 * V + q] = pr;
 }
 
 template <int P, int NP, bool NU, bool WALL>
@@ -780,6 +789,7 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
     const T u[3] = {a.u_out[q], a.u_out[V + q], a.u_out[2 * V + q]};
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T p0 = (T)p0d;
+    if constexpr (Prec<P>::REF) a.u_out[3 * V + q] = p0;
     for (int k = 1; k < 15; ++k) {
       const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
       const T geq = w3_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
@@ -788,8 +798,9 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
         const T sux = a.u_out[qs], suy = a.u_out[V + qs], suz = a.u_out[2 * V + qs];
         a.gm_out[(size_t)(k - 1) * V + q] = to_S<Sm>(
             geq * (a.sg_st / w3_of<T>(k)) -
-            (Prec<P>::REF ? g_ref3(cdotu3(k, sux, suy, suz), sux, suy, suz,
-                                   a.rho_base * a.sg_st)
+            // every source starts at p0 (stored as its p(t-1) above)
+            (Prec<P>::REF ? g_ref3p(cdotu3(k, sux, suy, suz), sux, suy, suz, p0,
+                                    a.rho_base * a.sg_st, T(3) * a.sg_st)
                           : T(0)));
       } else
         a.gm_out[(size_t)(k - 1) * V + q] = geq;

@@ -61,7 +61,8 @@ struct Grid {
   void *hm[2];      // moving populations h^i_k, k = 1..8: [N-1][8][V]
   void *gm[2];      // NS populations g_k, k = 1..8: [8][V]
   void *phi_prev[2];  // phi_i(t-1): [N-1][V]
-  void *u_prev[2];  // u(t-1): [D][V], ping-pong like phi_prev
+  void *u_prev[2];  // u(t-1): [D][V] (16-bit forms: [D + 1][V], p(t-1) last),
+                    // ping-pong like phi_prev
   double *red;      // per-block partial sums of the diagnostics
   double *red_out;  // N + 2 reduced diagnostics
   int *err;         // device error word (1: a bounded wait gave up)

@@ -7,6 +7,7 @@
 //   gm[k-1][V]      NS populations g_k, k = 1..8 (g_0 never influences u, p
 //                   or phi: u has c_0 = 0 and Eq. N23 sums k >= 1)
 //   phi_prev[2][i][V]   phi_i(t-1) (Eq. N27), ping-pong; u_prev[2][2][V] the same
+//                   for u(t-1) (16-bit forms: [2][3][V], p(t-1) third)
 // The stored populations are post-streaming values at their node (push
 // scheme), so phi_i(x) = sum_k h^i_k(x) is local (Eq. N28).
 //
@@ -239,6 +240,15 @@ __device__ __forceinline__ double g_ref(double cu, double ux, double uy,
                                         double srho) {
   return (3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy)) * srho;
 }
+// The same plus the pressure part 3 s p of the equilibrium; s3 = 3 s.
+__device__ __forceinline__ float g_refp(float cu, float ux, float uy, float p,
+                                        float srho, float s3) {
+  return __fadd_rn(g_ref(cu, ux, uy, srho), __fmul_rn(p, s3));
+}
+__device__ __forceinline__ double g_refp(double cu, double ux, double uy,
+                                         double p, double srho, double s3) {
+  return g_ref(cu, ux, uy, srho) + p * s3;
+}
 
 // The node slot k of (x, y) was streamed from: (x, y) - c_k, periodic in x
 // (and in y without walls); behind a wall, (x, y) itself.
@@ -283,8 +293,10 @@ __device__ __forceinline__ void load_g_node(const KArgs<P> &a, int x, int y,
     T v = load_gm<P>(a, k, q);
     if constexpr (Prec<P>::REF) {
       const size_t qs = source_node<WALL>(x, y, k, a.nx, a.ny);
-      const T sux = ldg(a.u_in + qs), suy = ldg(a.u_in + a.V + qs);
-      v = __fadd_rn(v, g_ref(cdotu(k, sux, suy), sux, suy, a.rho_base * a.sg_st));
+      const T sux = ldg(a.u_in + qs), suy = ldg(a.u_in + a.V + qs),
+              spr = ldg(a.u_in + 2 * a.V + qs);
+      v = __fadd_rn(v, g_refp(cdotu(k, sux, suy), sux, suy, spr, a.rho_base * a.sg_st,
+                              T(3) * a.sg_st));
     }
     g[k] = v;
   }
@@ -601,7 +613,7 @@ __device__ __forceinline__ void collide_stream(
     if constexpr (Prec<P>::REF)
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] = to_S<typename Prec<P>::Sm>(
           keep_g * g[k] + a.sg_st * t -
-          g_ref(cdotu(kk, ux, uy), ux, uy, a.rho_base * a.sg_st));
+          g_refp(cdotu(kk, ux, uy), ux, uy, pr, a.rho_base * a.sg_st, T(3) * a.sg_st));
     else if constexpr (MIX)
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] =
           to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
@@ -662,6 +674,7 @@ __device__ __forceinline__ void collide_stream(
   }
   a.u_out[q] = ux;
   a.u_out[V + q] = uy;
+  if constexpr (Prec<P>::REF) a.u_out[2 * V + q] = pr;
 }
 
 // Position of ring entry r of a (BX + 2R) x (BY + 2R) tile: top R rows,
@@ -899,6 +912,7 @@ template <int P> struct TmaGeom {
   static constexpr int UW = REF ? WR : BX;          // u(t-1) box
   static constexpr int UH = REF ? HBP : TBY;
   static constexpr int UOX = REF ? HXR : 0, UOY = REF ? RY : 0;
+  static constexpr int UPN = REF ? 3 : 2;           // u(t-1) planes (+ p(t-1))
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -952,7 +966,7 @@ template <int P, int NP> struct TmaStage {
   static constexpr size_t H0 = al((size_t)NP * G::HB * G::WR * sizeof(T));
   static constexpr size_t PP = al((size_t)NP * G::HBP * G::WR * sizeof(T));
   static constexpr size_t GM = al((size_t)8 * G::TBY * BX * sizeof(Sm));
-  static constexpr size_t UP = al((size_t)2 * G::UH * G::UW * sizeof(T));
+  static constexpr size_t UP = al((size_t)G::UPN * G::UH * G::UW * sizeof(T));
   static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
   // bytes the TMA engine writes per stage (full boxes, including fill)
   static constexpr uint32_t TX =
@@ -960,7 +974,7 @@ template <int P, int NP> struct TmaStage {
                  (size_t)NP * G::HB * G::WR * sizeof(T) +
                  (size_t)NP * G::HBP * G::WR * sizeof(T) +
                  (size_t)8 * G::TBY * BX * sizeof(Sm) +
-                 (size_t)2 * G::UH * G::UW * sizeof(T));
+                 (size_t)G::UPN * G::UH * G::UW * sizeof(T));
   static constexpr size_t SPHI = al((size_t)NP * (G::TBY + 2) * (BX + 2) * sizeof(T));
   static constexpr int S = G::S;
   static constexpr size_t SMEM = S * BYTES + SPHI + 64;
@@ -1044,11 +1058,12 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
     // wall) find every source in the boxes at a fixed offset.
     const bool inner = x0 >= 2 && x0 + BX + 2 <= nx && y0 >= 2 && y0 + TBY + 2 <= ny;
     auto source = [&](int k, int xn, int yn, int cb, int rb, T &sux, T &suy,
-                      T *sph) {
+                      T &spr, T *sph) {
       if (inner) {
         const int o = (rb - cy_of(k)) * G::UW + cb - cx_of(k);
         sux = sup[o];
         suy = sup[G::UH * G::UW + o];
+        spr = sup[2 * G::UH * G::UW + o];
 #pragma unroll
         for (int i = 0; i < NP; ++i)
           sph[i] = spp[(i * G::HBP + rb - cy_of(k)) * G::WR + cb - cx_of(k)];
@@ -1062,17 +1077,19 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
       if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) {
         sux = sup[r * G::UW + c];
         suy = sup[(G::UH + r) * G::UW + c];
+        spr = sup[(2 * G::UH + r) * G::UW + c];
 #pragma unroll
         for (int i = 0; i < NP; ++i) sph[i] = spp[(i * G::HBP + r) * G::WR + c];
       } else {
         const size_t qs = source_node<WALL>(xn, yn, k, nx, ny);
         sux = ldg(a.u_in + qs);
         suy = ldg(a.u_in + a.V + qs);
+        spr = ldg(a.u_in + 2 * a.V + qs);
 #pragma unroll
         for (int i = 0; i < NP; ++i) sph[i] = ldg(a.pp_in + (size_t)i * a.V + qs);
       }
     };
-    const T s3h = T(3) * a.sh_st, srg = a.rho_base * a.sg_st;
+    const T s3h = T(3) * a.sh_st, srg = a.rho_base * a.sg_st, s3g = T(3) * a.sg_st;
     // A thread whose wait gave up still runs the phi sums below (on stale
     // shared data, harmlessly); the barrier after them makes the decision
     // to stop the same for the whole CTA.
@@ -1091,8 +1108,8 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
         const int xn = x0 - G::HXR + bxr, yn = y0 - 1 + by;
 #pragma unroll
         for (int k = 1; k < 9; ++k) {
-          T sux, suy, sph[NP];
-          source(k, xn, yn, bxr, by - 1 + G::RY, sux, suy, sph);
+          T sux, suy, spr, sph[NP];
+          source(k, xn, yn, bxr, by - 1 + G::RY, sux, suy, spr, sph);
           const T cu = cdotu(k, sux, suy);
 #pragma unroll
           for (int i = 0; i < NP; ++i)
@@ -1127,13 +1144,13 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
       if constexpr (G::REF) {
 #pragma unroll
         for (int k = 1; k < 9; ++k) {
-          T sux, suy, sph[NP];
-          source(k, gx, gy, tx + G::HXR, ty + G::RY, sux, suy, sph);
+          T sux, suy, spr, sph[NP];
+          source(k, gx, gy, tx + G::HXR, ty + G::RY, sux, suy, spr, sph);
           const T cu = cdotu(k, sux, suy);
 #pragma unroll
           for (int i = 0; i < NP; ++i)
             hreg[i][k] = __fadd_rn(hreg[i][k], adv_units(cu, sph[i], s3h));
-          g[k] = __fadd_rn(g[k], g_ref(cu, sux, suy, srg));
+          g[k] = __fadd_rn(g[k], g_refp(cu, sux, suy, spr, srg, s3g));
         }
       }
 #pragma unroll
@@ -1250,6 +1267,7 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
     const T ux = a.u_out[q], uy = a.u_out[V + q];
     const T uu = ux * ux + uy * uy;
     const T p0 = (T)p0d;
+    if constexpr (Prec<P>::REF) a.u_out[2 * V + q] = p0;
 #pragma unroll
     for (int k = 1; k < 9; ++k) {
       const T cu = T(cx_of(k)) * ux + T(cy_of(k)) * uy;
@@ -1257,9 +1275,10 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
       if constexpr (Prec<P>::MIX) {
         const size_t qs = source_node<WALL>(x, y, k, nx, ny);
         const T sux = a.u_out[qs], suy = a.u_out[V + qs];
-        const T ref = Prec<P>::REF
-                          ? g_ref(cdotu(k, sux, suy), sux, suy, a.rho_base * a.sg_st)
-                          : T(0);
+        // every source starts at p0 (stored as its p(t-1) below)
+        const T ref = Prec<P>::REF ? g_refp(cdotu(k, sux, suy), sux, suy, p0,
+                                            a.rho_base * a.sg_st, T(3) * a.sg_st)
+                                   : T(0);
         gm[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w_of<T>(k)) - ref);
       } else
         gm[(size_t)(k - 1) * V + q] = geq;
@@ -1394,7 +1413,7 @@ bool encode_tma_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
                 enc3(&m.h0, g.h0[b], sizeof(T), NP, G::WR, G::HB, NP) &&
                 enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HBP, NP) &&
                 enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, G::TBY, 8) &&
-                enc3(&m.up, g.u_prev[b], sizeof(T), 2, G::UW, G::UH, 2);
+                enc3(&m.up, g.u_prev[b], sizeof(T), G::UPN, G::UW, G::UH, G::UPN);
       if (!ok) return false;
     }
     return true;
