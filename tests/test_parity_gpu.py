@@ -227,8 +227,10 @@ def test_precision_forms_error(prec):
 # max |dphi|, max |du| / max |u|, centre-of-mass shift (nodes) allowed
 # after 2000 steps of the 512x512 collision; every form meets the 1e-3
 # target on phi (measured 3.4e-4, 8.3e-4, 3.2e-4).
-COLLISION_BOUNDS = {"fp32": (1e-3, 1e-3, 1e-2), "fp16": (1e-3, 5e-3, 1e-2),
-                    "bf16": (1e-3, 1e-2, 5e-2)}
+# (max |dphi|, max |du| / max |u|, drop centres in nodes); measured
+# FP32 3.4e-4 / 1.8e-4, FP16 3.3e-4 / 1.8e-4, BF16 3.4e-4 / 1.9e-4
+COLLISION_BOUNDS = {"fp32": (1e-3, 1e-3, 1e-2), "fp16": (1e-3, 1e-3, 1e-2),
+                    "bf16": (1e-3, 1e-3, 5e-2)}
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
@@ -267,7 +269,7 @@ def droplets_2048_fp64_1e4():
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_droplets_2048_precision_forms_1e4_steps(droplets_2048_fp64_1e4, prec):
     """The benchmarked workload over 1e4 steps in each reduced-precision
-    form: max |dphi| <= 1e-3 against FP64 (measured 1.9e-4, 5.9e-4, 6.0e-4),
+    form: max |dphi| <= 1e-3 against FP64 (measured 1.9e-4, 3.3e-4, 1.9e-4),
     per-phase mass within 1e-6 of FP64's."""
     w, (ref, rd) = droplets_2048_fp64_1e4
     g, gd = gpu_run(w, 10000, prec=prec, diag=True)
