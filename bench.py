@@ -255,7 +255,8 @@ def e2e_run(w, prec, steps):
 def d3q15_run(n=256, steps=100, prec="fp32"):
     """D3Q15 (three dimensions): three phases, two sphere drops R = n/6 in a
     periodic n^3 box, z-marching 3-D kernel; FP32 storage, or 16-bit
-    storage relative to the velocity part of the equilibrium."""
+    storage relative to the advective and pressure parts of the
+    equilibrium."""
     import torch
     from paper_1904_12553_gb300 import Solver, workloads as W
 

@@ -78,10 +78,11 @@ __device__ __forceinline__ typename Prec<P>::T load_hm3(const KArgs<P> &a, int i
   return to_T(ldg(a.hm_in + ((size_t)(i * 14 + k - 1)) * a.V + q));
 }
 
-// 16-bit forms store every moving population relative to the velocity part
-// of its equilibrium at the node it was streamed from, as in two dimensions
-// (cdotu, adv_units, g_ref there): c_k . u with the same rounded operations
-// on writer and reader (D3Q15 has face and corner velocities only).
+// 16-bit forms store every moving population relative to the advective (and
+// for g the pressure) part of its equilibrium at the node it was streamed
+// from, as in two dimensions (cdotu, adv_units, g_refp there): c_k . u with
+// the same rounded operations on writer and reader (D3Q15 has face and corner
+// velocities only).
 __device__ __forceinline__ float cdotu3(int k, float ux, float uy, float uz) {
   const int cx = c3x(k), cy = c3y(k), cz = c3z(k);
   const float a = cx > 0 ? ux : -ux, b = cy > 0 ? uy : -uy, c = cz > 0 ? uz : -uz;
@@ -424,7 +425,7 @@ __device__ __forceinline__ void collide3(
       const T hk = o.h[i][k];
       const size_t oo = ((size_t)(i * 14 + dk[k] - 1)) * V + dst[k];
       if constexpr (MIX) {
-        // relative to the velocity part at this node, the slot's source
+        // relative to the advective part at this node, the slot's source
         const T ref = Prec<P>::REF
                           ? adv_units(cdotu3(dk[k], u[0], u[1], u[2]), ph[i], T(3) * a.sh_st)
                           : T(0);

@@ -60,9 +60,10 @@ static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 &&
 
 // Storage policy per precision. MIX: 16-bit moving populations in stored
 // units s f_k / w_k. REF: stored relative to the advective part of their
-// equilibrium at their source node (both 16-bit forms: without it BF16 misses
-// the 1e-3 phi target on colliding drops by 13x and FP16 on a resting lens by
-// up to 5x).
+// equilibrium (for g also its pressure part) at their source node (both
+// 16-bit forms: without it BF16 misses the 1e-3 phi target on colliding drops
+// by 13x and FP16 on a resting lens by up to 5x; without the pressure part
+// BF16 drifts past it on small resting drops).
 template <int P> struct Prec;
 template <> struct Prec<LBM_FP64> {
   typedef double T;
@@ -201,17 +202,18 @@ __device__ __forceinline__ typename Prec<P>::T load_gm(const KArgs<P> &a, int k,
   return to_T(ldg(a.gm_in + ((size_t)(k - 1)) * a.V + q));
 }
 
-// 16-bit forms: every moving population is stored relative to the velocity
-// part of its equilibrium (Eqs. 25, N25) evaluated at the node it was
-// streamed from: slot k of node y holds
-//     s h_k / w_k - 3 s (c_k . u) phi_i                          (h, phase i)
-//     s g_k / w_k - s rho~ (3 c_k.u + 4.5 (c_k.u)^2 - 1.5 |u|^2)  (g)
+// 16-bit forms: every moving population is stored relative to part of its
+// equilibrium (Eqs. 25, N25) evaluated at the node it was streamed from:
+// slot k of node y holds
+//     s h_k / w_k - 3 s (c_k . u) phi_i                               (h, phase i)
+//     s g_k / w_k - s (3 p + rho~ (3 c_k.u + 4.5 (c_k.u)^2 - 1.5 |u|^2))  (g)
 // (rho~ = the constant N/Gamma)
-// with u = u(t), phi = phi(t) of the source node y - c_k (of y itself when
-// y - c_k lies behind a wall: the slot was filled by bounce-back). The writer
-// uses its own u(t), phi(t); the reader takes them as u(t-1), phi(t-1) of the
-// source. The subtracted part is the bulk of a population in a moving flow,
-// so the 16-bit value keeps its significant bits for the rest. Both sides
+// with u = u(t), p = p(t), phi = phi(t) of the source node y - c_k (of y
+// itself when y - c_k lies behind a wall: the slot was filled by bounce-back).
+// The writer uses its own u(t), p(t), phi(t); the reader takes them as
+// u(t-1), p(t-1), phi(t-1) of the source. The subtracted part is the bulk of
+// a population (in a moving flow the advective part; at rest 3p of g), so
+// the 16-bit value keeps its significant bits for the rest. Both sides
 // compute it with the same rounded operations (no contraction), so a value
 // decodes to exactly what its writer counted in the node's mass balance.
 __device__ __forceinline__ float cdotu(int k, float ux, float uy) {

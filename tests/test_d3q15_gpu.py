@@ -123,7 +123,7 @@ MOVING3 = {0: dict(seed=5, N=4, shape=(32, 24, 28)),
 @pytest.mark.parametrize("prec,bound", [("bf16", 3e-4), ("fp16", 3e-5)])
 @pytest.mark.parametrize("wall", [0, 1])
 def test_d3q15_16bit_moving_flow(prec, bound, wall):
-    """16-bit storage relative to the velocity part of the equilibrium in a
+    """16-bit storage relative to the source's equilibrium parts in a
     moving 3-D flow (|u| up to 0.02 at start), 2000 steps against the FP64
     GPU path (itself pinned to the oracle above). Measured 4.6e-5 / 7.9e-5
     (BF16) and 5.7e-6 / 3.1e-6 (FP16); plain storage of the populations gave
