@@ -281,7 +281,8 @@ int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h);
 /* Which kernel lbm_nphase_step runs for this handle: 1 the TMA-pipelined
  * D2Q9 kernel (FP32 and 16-bit forms, equal pure-phase densities, nx a
  * multiple of 8), 2 the z-marching D3Q15 kernel (equal densities, every
- * storage form), 0 the generic tile kernel. Setting the environment variable
+ * storage form), 3 the z-marching D3Q15 kernel with TMA-staged planes (FP32,
+ * equal densities, N <= 4, nx a multiple of 4), 0 the generic tile kernel. Setting the environment variable
  * LBM_NPHASE_KERNEL=generic before lbm_nphase_create selects the generic
  * kernels everywhere. All compute the same step. */
 int lbm_nphase_uses_pipelined_kernel(const lbm_nphase_t *h);

@@ -374,7 +374,8 @@ class Solver:
 
     @property
     def step_kernel(self) -> str:
-        return {1: "pipelined (TMA)", 2: "z-marching 3-D"}.get(
+        return {1: "pipelined (TMA)", 2: "z-marching 3-D",
+                3: "z-marching 3-D (TMA)"}.get(
             lbm_nphase_uses_pipelined_kernel(self.handle), "generic tile")
 
     @property

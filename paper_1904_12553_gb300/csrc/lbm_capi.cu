@@ -502,6 +502,8 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   g.grad_scheme = p->grad_scheme;
   g.use_tma = false;
   g.march3 = tma_allowed() && !h->nonunif && p->lattice == 1;
+  g.tma3 = g.march3 && h->prec == LBM_FP32 &&
+           lbm::encode_tma3_f32(k, g, tensor_map_encoder());
   if (tma_allowed() && !h->nonunif && p->grad_scheme == 0 && p->lattice == 0) {
     lbm::EncodeTiledFn enc = tensor_map_encoder();
     switch (h->prec) {
@@ -802,7 +804,7 @@ lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
 
 int lbm_nphase_uses_pipelined_kernel(const lbm_nphase_t *h) {
   if (!h) return 0;
-  return h->g.use_tma ? 1 : (h->g.march3 ? 2 : 0);
+  return h->g.use_tma ? 1 : (h->g.tma3 ? 3 : (h->g.march3 ? 2 : 0));
 }
 
 int64_t lbm_nphase_steps_taken(const lbm_nphase_t *h) { return h ? h->steps : 0; }

@@ -654,6 +654,37 @@ __device__ __forceinline__ void stencil3w(const T *pm, const T *p0, const T *pp,
   lap = T(6) * l;
 }
 
+// The step of one node of plane z from the phi window (planes z - 1, z, z + 1
+// with the xy ring, stride SW) and the node's own values (equal densities).
+template <int P, int NP, bool WALL, int SW, int PL>
+__device__ __forceinline__ void march3_node(
+    const KArgs<P> &a, int nz, const typename Prec<P>::T (*wm)[PL],
+    const typename Prec<P>::T (*w0)[PL], const typename Prec<P>::T (*wp)[PL],
+    int tx, int ty, const Own3<P, NP> &own, size_t q, int gx, int gy, int z) {
+  typedef typename Prec<P>::T T;
+  T ph[NP], gp[NP][3], Cv[NP], cc[NP + 1], rho;
+  {
+    T lp[NP], hf[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      ph[i] = w0[i][(ty + 1) * SW + tx + 1];
+      stencil3w<T, SW>(wm[i], w0[i], wp[i], ty + 1, tx + 1, gp[i], lp[i]);
+    }
+    local_algebra<P, NP, true>(a, ph, cc, rho, hf);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T Ci = a.bulk * hf[i];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
+      Cv[i] = Ci;
+    }
+  }
+  const T gr[3] = {T(0), T(0), T(0)}, J[3] = {T(0), T(0), T(0)};
+  T F[3], u[3], uu, pr;
+  macros3<P, NP>(a, gp, Cv, rho, gr, own.g, u, F, uu, pr);
+  collide3<P, NP, false, WALL>(a, nz, ph, Cv, rho, gr, J, own, u, F, uu, pr, q, gx, gy, z);
+}
+
 template <int P, int NP, bool WALL>
 __global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
     march3_kernel(const KArgs3<P> A, int zlen) {
@@ -713,34 +744,193 @@ __global__ void __launch_bounds__(MT3, P == LBM_FP64 ? 1 : 2)
     load_own3c<P, NP>(a, q, ocache + tid, MT3, own);
     plane_phi(z + 1);
     __syncthreads();
-    if (col) {
-      const T(*wm)[PL] = win[slot(z - 1)];
-      const T(*w0)[PL] = win[slot(z)];
-      const T(*wp)[PL] = win[slot(z + 1)];
-      T ph[NP], gp[NP][3], Cv[NP], cc[NP + 1], rho;
-      {
-        T lp[NP], hf[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          ph[i] = w0[i][(ty + 1) * SW + tx + 1];
-          stencil3w<T, SW>(wm[i], w0[i], wp[i], ty + 1, tx + 1, gp[i], lp[i]);
-        }
-        local_algebra<P, NP, true>(a, ph, cc, rho, hf);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          T Ci = a.bulk * hf[i];
-#pragma unroll
-          for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
-          Cv[i] = Ci;
-        }
-      }
-      const T gr[3] = {T(0), T(0), T(0)}, J[3] = {T(0), T(0), T(0)};
-      T F[3], u[3], uu, pr;
-      macros3<P, NP>(a, gp, Cv, rho, gr, own.g, u, F, uu, pr);
-      collide3<P, NP, false, WALL>(a, nz, ph, Cv, rho, gr, J, own, u, F, uu, pr,
-                                   q, gx, gy, z);
-    }
+    if (col)
+      march3_node<P, NP, WALL, SW, PL>(a, nz, win[slot(z - 1)], win[slot(z)],
+                                       win[slot(z + 1)], tx, ty, own, q, gx, gy, z);
     __syncthreads();  // plane z - 1's slot is refilled next
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The z-marching step with its planes staged by TMA (FP32, N <= 4, nx a
+// multiple of 4): per plane one 4-D box per array, the column with one halo
+// row and four halo columns (h^i_k, d^i_0, phi_i(t-1)) or the column alone
+// (g_k, u(t-1)), into two stages; the boxes of plane z + 2 load while plane
+// z + 1's phi is summed and plane z stepped. Ring positions that wrap around
+// the grid (or lie on a wall's ghost row) and columns that overhang it read
+// global memory; everything else comes from the stage, with the same
+// arithmetic as march3_kernel. One CTA of 8 warps per SM.
+// ---------------------------------------------------------------------------
+template <int P, int NP> struct March3Stage {
+  typedef typename Prec<P>::T T;
+  static constexpr int HX = 16 / (int)sizeof(T);  // halo columns (16-byte TMA x)
+  static constexpr int BW = MX3 + 2 * HX, BH = MY3 + 2;
+  static constexpr size_t al(size_t b) { return (b + 127) & ~(size_t)127; }
+  static constexpr size_t HM = al((size_t)NP * 14 * BH * BW * sizeof(T));
+  static constexpr size_t H0 = al((size_t)NP * BH * BW * sizeof(T));
+  static constexpr size_t PP = H0;
+  static constexpr size_t GM = al((size_t)14 * MY3 * MX3 * sizeof(T));
+  static constexpr size_t UP = al((size_t)3 * MY3 * MX3 * sizeof(T));
+  static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
+  static constexpr uint32_t TX =
+      (uint32_t)(((size_t)NP * 16 * BH * BW + (size_t)17 * MY3 * MX3) * sizeof(T));
+  static constexpr size_t WIN = (size_t)3 * NP * (MX3 + 2) * (MY3 + 2) * sizeof(T);
+  static constexpr size_t SMEM = 2 * BYTES + WIN + 16;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+};
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x,
+                                            int y, int z, int w, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int P, int NP, bool WALL>
+__global__ void __launch_bounds__(MT3, 1)
+    march3_tma_kernel(const KArgs3<P> A, const __grid_constant__ TmaMaps maps, int zlen) {
+  typedef typename Prec<P>::T T;
+  typedef March3Stage<P, NP> St;
+  const KArgs<P> &a = A.a;
+  constexpr int SW = MX3 + 2, SH = MY3 + 2, PL = SW * SH;
+  constexpr int BW = St::BW, BH = St::BH, HX = St::HX;
+  extern __shared__ __align__(128) unsigned char smem_t3[];
+  T(*win)[NP][PL] = (T(*)[NP][PL])(smem_t3 + 2 * St::BYTES);
+  uint64_t *bar = (uint64_t *)(smem_t3 + 2 * St::BYTES + St::WIN);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MX3 + tx;
+  const int nx = a.nx, ny = a.ny, nz = A.nz;
+  const int x0 = blockIdx.x * MX3, y0 = blockIdx.y * MY3;
+  const int zs = blockIdx.z * zlen;
+  const int ze = zs + zlen < nz ? zs + zlen : nz;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool col = gx < nx && gy < ny;
+  auto slot = [&](int z) { return (z - zs + 1) % 3; };
+  // stage and barrier of plane p >= zs; the barrier's k-th completion
+  // (parity k & 1) is the k-th plane loaded into that stage
+  auto stage = [&](int p) { return smem_t3 + ((p - zs) & 1) * St::BYTES; };
+  auto issue = [&](int p) {  // thread 0
+    unsigned char *st = stage(p);
+    uint64_t *b = bar + ((p - zs) & 1);
+    const int pz = wrap(p, nz);
+    mbar_expect_tx(b, St::TX);
+    tma_load_4d(st, &maps.hm, x0 - HX, y0 - 1, pz, 0, b);
+    tma_load_4d(st + St::HM, &maps.h0, x0 - HX, y0 - 1, pz, 0, b);
+    tma_load_4d(st + St::HM + St::H0, &maps.pp, x0 - HX, y0 - 1, pz, 0, b);
+    tma_load_4d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, pz, 0, b);
+    tma_load_4d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0, y0, pz, 0, b);
+  };
+  auto wait = [&](int p) {
+    return mbar_wait(bar + ((p - zs) & 1), (uint32_t)(((p - zs) >> 1) & 1));
+  };
+  // phi at box position (bx, by) of a stage, summed as in node_phis3
+  auto box_phis = [&](const unsigned char *st, int bx, int by, T(&phv)[NP]) {
+    const T *hm = (const T *)st, *h0 = (const T *)(st + St::HM),
+            *pp = (const T *)(st + St::HM + St::H0);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T small = h0[(i * BH + by) * BW + bx];
+#pragma unroll
+      for (int k = 1; k < 15; ++k)
+        small = __fadd_rn_T(small, hm[((i * 14 + k - 1) * BH + by) * BW + bx]);
+      phv[i] = __fadd_rn(pp[(i * BH + by) * BW + bx], small);
+    }
+  };
+  // phi of plane z on the tile and its xy ring, from global memory (plane
+  // zs - 1) or from the stage (planes zs .. ze)
+  auto plane_phi = [&](int z, bool staged) {
+    T(*w)[PL] = win[slot(z)];
+    const int zz = wrap(z, nz);
+    {
+      T phv[NP];
+      if (staged && col) {
+        box_phis(stage(z), tx + HX, ty + 1, phv);
+      } else {
+        const int cx = wrap(gx, nx), cy = wrap_y<WALL>(gy, ny);
+        node_phis3<P, NP, WALL>(a, nz, cx, cy, zz, ((size_t)zz * ny + cy) * nx + cx, phv);
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) w[i][(ty + 1) * SW + tx + 1] = phv[i];
+    }
+    constexpr int NRING = PL - MT3;
+    static_assert(NRING <= MT3, "one ring position per thread");
+    if (tid < NRING) {
+      int lx, ly;
+      ring_pos_1<MY3>(tid, lx, ly);
+      const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
+      T phv[NP];
+      if (staged && X >= 0 && X < nx && Y >= 0 && Y < ny) {
+        box_phis(stage(z), lx - 1 + HX, ly, phv);
+      } else {
+        const int rx = wrap(X, nx), ry = wrap_y<WALL>(Y, ny);
+        node_phis3<P, NP, WALL>(a, nz, rx, ry, zz, ((size_t)zz * ny + ry) * nx + rx, phv);
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) w[i][ly * SW + lx] = phv[i];
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    issue(zs);
+    if (zs + 1 <= ze) issue(zs + 1);
+  }
+  __syncthreads();
+  plane_phi(zs - 1, false);
+  bool ok = wait(zs);
+  plane_phi(zs, true);
+  int failed_at = -1;
+  for (int z = zs; z < ze; ++z) {
+    // own values of plane z from its stage, then the stage is free for
+    // plane z + 2 once every thread has read it
+    Own3<P, NP> own;
+    if (col) {
+      const unsigned char *st = stage(z);
+      const T *hm = (const T *)st, *h0 = (const T *)(st + St::HM),
+              *pp = (const T *)(st + St::HM + St::H0),
+              *gm = (const T *)(st + St::HM + St::H0 + St::PP),
+              *up = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
+      const int o = (ty + 1) * BW + tx + HX;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        own.h[i][0] = h0[i * BH * BW + o];
+#pragma unroll
+        for (int k = 1; k < 15; ++k) own.h[i][k] = hm[(i * 14 + k - 1) * BH * BW + o];
+        own.pp[i] = pp[i * BH * BW + o];
+      }
+#pragma unroll
+      for (int k = 1; k < 15; ++k) own.g[k] = gm[((k - 1) * MY3 + ty) * MX3 + tx];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) own.up[d] = up[(d * MY3 + ty) * MX3 + tx];
+    }
+    __syncthreads();
+    if (tid == 0 && z + 2 <= ze) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(z + 2);
+    }
+    ok = wait(z + 1) && ok;
+    plane_phi(z + 1, true);
+    // phi of plane z + 1 complete, and the decision to stop CTA-wide
+    if (__syncthreads_or(!ok)) {
+      failed_at = z;
+      break;
+    }
+    if (col)
+      march3_node<P, NP, WALL, SW, PL>(a, nz, win[slot(z - 1)], win[slot(z)],
+                                       win[slot(z + 1)], tx, ty, own,
+                                       ((size_t)z * ny + gy) * nx + gx, gx, gy, z);
+  }
+  if (failed_at >= 0 || !ok) {
+    // record the timeout and let the loads still in flight land (bounded)
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      const int last = failed_at + 2 <= ze ? failed_at + 2 : ze;
+      for (int p = (failed_at >= 0 ? failed_at + 1 : zs); p <= last; ++p) wait(p);
+    }
+    __syncthreads();
   }
 }
 
@@ -854,6 +1044,22 @@ cudaError_t launch_tile3_t(const Consts &c, const Grid &g, int cur, int mode,
       if (zl > g.nz) zl = g.nz;
       const int zlen = (int)zl;
       dim3 grid(tiles_x(g.nx), (g.ny + MY3 - 1) / MY3, (g.nz + zlen - 1) / zlen);
+      if constexpr (P == LBM_FP32 && NP <= 3) {
+        if (g.tma3) {
+          typedef March3Stage<P, NP> St;
+          static bool tattr = false;
+          if (!tattr) {
+            cudaError_t e = cudaFuncSetAttribute(march3_tma_kernel<P, NP, WALL>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)St::SMEM);
+            if (e != cudaSuccess) return e;
+            tattr = true;
+          }
+          march3_tma_kernel<P, NP, WALL><<<grid, dim3(MX3, MY3), St::SMEM, s>>>(
+              A, *(const TmaMaps *)&g.tma[cur], zlen);
+          return cudaGetLastError();
+        }
+      }
       constexpr size_t msm = march3_smem<P, NP>();
       static bool mattr = false;
       if (!mattr) {
@@ -893,6 +1099,42 @@ cudaError_t launch_tile3_np(const Consts &c, const Grid &g, int cur, int mode,
                 : launch_tile3_t<P, NP, true, false>(c, g, cur, mode, o, s);
   return wall ? launch_tile3_t<P, NP, false, true>(c, g, cur, mode, o, s)
               : launch_tile3_t<P, NP, false, false>(c, g, cur, mode, o, s);
+}
+
+// Tensor maps of the TMA z-marching kernel for both state buffers: each
+// array as a 4-D tensor (x, y, z, plane); FP32 with 2 to 4 phases and nx a
+// multiple of 4 (16-byte row pitch) only.
+template <int P>
+bool encode_tma3_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
+  if constexpr (P != LBM_FP32) {
+    return false;
+  } else {
+    const int NP = c.NP;
+    if (!enc || NP < 1 || NP > 3 || g.nx % 4 != 0) return false;
+    typedef March3Stage<P, 1> S1;
+    auto enc4 = [&](CUtensorMap *m, void *base, int planes, int bw, int bh) {
+      const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                                  (cuuint64_t)planes};
+      const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4,
+                                     (cuuint64_t)g.V * 4};
+      const cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 1, (cuuint32_t)planes};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int b = 0; b < 2; ++b) {
+      TmaMaps &m = *(TmaMaps *)&g.tma[b];
+      const bool ok = enc4(&m.hm, g.hm[b], 14 * NP, S1::BW, S1::BH) &&
+                      enc4(&m.h0, g.h0[b], NP, S1::BW, S1::BH) &&
+                      enc4(&m.pp, g.phi_prev[b], NP, S1::BW, S1::BH) &&
+                      enc4(&m.gm, g.gm[b], 14, MX3, MY3) &&
+                      enc4(&m.up, g.u_prev[b], 3, MX3, MY3);
+      if (!ok) return false;
+    }
+    return true;
+  }
 }
 
 template <int P>

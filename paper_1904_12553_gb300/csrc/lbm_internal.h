@@ -69,6 +69,7 @@ struct Grid {
   int grad_scheme;  // 0: central (Eq. N31a), 1: mixed (Eq. N40)
   bool use_tma;     // pipelined kernel usable for this grid
   bool march3;      // D3Q15 step by the z-marching kernel
+  bool tma3;        // ... with its planes staged by TMA (tma[] holds 4-D maps)
   TmaMaps tma[2];   // its descriptors, input buffer 0 or 1
 };
 
@@ -93,6 +94,7 @@ cudaError_t launch_reduce(const Grid &g, int nparts, int nvals, cudaStream_t s);
                                    const double *, const double *, double,    \
                                    bool, cudaStream_t);                       \
   bool encode_tma_##SUFFIX(const Consts &, Grid &, EncodeTiledFn);           \
+  bool encode_tma3_##SUFFIX(const Consts &, Grid &, EncodeTiledFn);          \
   cudaError_t launch_tile3_##SUFFIX(const Consts &, const Grid &, int, int,   \
                                     const Outputs &, bool, bool, cudaStream_t);\
   cudaError_t launch_init3_##SUFFIX(const Consts &, const Grid &, int,        \

@@ -1475,6 +1475,9 @@ cudaError_t launch_init_p(const Consts &c, const Grid &g, int cur,
   bool encode_tma_##SUFFIX(const Consts &c, Grid &g, EncodeTiledFn enc) {      \
     return encode_tma_p<P>(c, g, enc);                                         \
   }                                                                            \
+  bool encode_tma3_##SUFFIX(const Consts &c, Grid &g, EncodeTiledFn enc) {     \
+    return encode_tma3_p<P>(c, g, enc);                                        \
+  }                                                                            \
   cudaError_t launch_tile3_##SUFFIX(const Consts &c, const Grid &g, int cur,   \
                                     int mode, const Outputs &o, bool nonunif,  \
                                     bool wall, cudaStream_t s) {               \
