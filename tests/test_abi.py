@@ -177,6 +177,28 @@ def test_workspace_bytes_scale(lib):
         {**p, "precision": "fp32"})
 
 
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_16bit_workspace_holds_p_prev(lib, lattice):
+    """The 16-bit forms keep p(t-1) as one more plane of the u(t-1)
+    ping-pong buffers (their g storage is relative to it). On a grid whose
+    sections need no alignment padding, FP32 minus BF16 workspace is exactly
+    the halved moving populations less that plane:
+    2 x (Q-1)(N-1+1) x V x 2 bytes - 2 x V x 4 bytes."""
+    N, nx, ny, nz = 3, 64, 64, 8
+    if lattice == 0:
+        p = W.base_params(N, nx, ny, 1e-3)
+        V, QM = nx * ny, 8
+    else:
+        p = W.base_params3(N, nx, ny, nz, 1e-3)
+        V, QM = nx * ny * nz, 14
+    b32 = P.lbm_nphase_workspace_bytes({**p, "precision": "fp32"})
+    b16 = P.lbm_nphase_workspace_bytes({**p, "precision": "bf16"})
+    bh = P.lbm_nphase_workspace_bytes({**p, "precision": "fp16"})
+    assert b16 == bh
+    moving = QM * (N - 1) + QM
+    assert b32 - b16 == 2 * moving * V * 2 - 2 * V * 4
+
+
 def test_create_rejects_bad_workspace(lib):
     p = W.static_drops().params
     with pytest.raises(P.LbmError) as e:
