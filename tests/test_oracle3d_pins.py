@@ -181,3 +181,22 @@ def test_flat_interface_along_z():
             assert np.ptp(m["c"], axis=(2, 3)).max() < 1e-14
     assert drifts[0] < 1e-2 and drifts[1] < 1e-3, drifts
     assert drifts[0] / drifts[1] > 4.0, drifts
+
+
+def test_uniform_flow3_is_preserved():
+    """A uniform mixture moving at constant velocity stays at equilibrium on
+    D3Q15: u is kept in all three components and the fields stay uniform
+    (Eq. N22_1, the third-order equilibrium moments and streaming)."""
+    N, sh = 3, (5, 6, 7)
+    c = np.broadcast_to(np.array([0.2, 0.5, 0.3])[:, None, None, None], (N,) + sh).copy()
+    u0 = np.zeros((3,) + sh)
+    u0[0], u0[1], u0[2] = 0.03, -0.02, 0.015
+    p = W.base_params3(N, sh[2], sh[1], sh[0], 1e-3, rho=[1.0, 4.0, 2.0])
+    s = oracle.OracleSim3D(p)
+    s.init(c, u0)
+    s.step(200)
+    m = s.moments()
+    for d, v in enumerate((0.03, -0.02, 0.015)):
+        np.testing.assert_allclose(m["u"][d], v, atol=1e-15)
+    assert np.ptp(m["phi"], axis=(1, 2, 3)).max() <= 1e-14
+    s.close()
