@@ -200,3 +200,16 @@ def test_uniform_flow3_is_preserved():
         np.testing.assert_allclose(m["u"][d], v, atol=1e-15)
     assert np.ptp(m["phi"], axis=(1, 2, 3)).max() <= 1e-14
     s.close()
+
+
+def test_rho0_is_inert3():
+    """On D3Q15 too, rho_0 of Eq. 25 reaches only g_0, which enters neither u
+    (c_0 = 0) nor p (Eq. N23 sums k >= 1): outputs are bit-identical."""
+    w = W.random_smooth3(9, 3, 8, 7, 6, rho=[2.0, 1.0, 5.0], amp_u=0.01)
+    outs = []
+    for r0 in (0.0, 1.0, 7.0):
+        p = dict(w.params, rho0=r0)
+        outs.append(oracle.run3(p, w.c0, w.u0, steps=30))
+    for o in outs[1:]:
+        for k in ("phi", "u", "p"):
+            assert np.array_equal(o[k], outs[0][k])
