@@ -328,6 +328,30 @@ def test_uniform_flow_is_preserved():
     s.close()
 
 
+@pytest.mark.parametrize("tau_g", [0.8, 1.0])
+def test_channel_flow_between_walls(tau_g):
+    """Halfway bounce-back (Section 4.2) puts the no-slip walls half a node
+    beyond the first and last fluid rows. A uniform mixture driven along x
+    by a body force rho g between them settles on the plane Poiseuille
+    parabola u(y) = g (y + 1/2)(ny - 1/2 - y) / (2 nu), nu = (tau_g - 1/2)/3
+    (Eq. N21_1), with no flow across: within 1% (0.20% and 0.13% when this
+    pin was written; the remainder is the halfway wall's second-order slip)."""
+    ny, nx, g = 16, 4, 1e-6
+    w = W.quiescent(3, nx, ny, frac=[0.2, 0.5, 0.3], wall_y=1)
+    p = dict(w.params, gravity=[g, 0.0], tau_g=tau_g)
+    s = oracle.OracleSim(p)
+    s.init(w.c0)
+    s.step(6000)                  # ~2.3 viscous times ny^2 / nu at tau_g 0.8
+    m = s.moments()
+    s.close()
+    nu = (tau_g - 0.5) / 3.0
+    y = np.arange(ny) + 0.5
+    ua = g * y * (ny - y) / (2.0 * nu)
+    for x in range(nx):
+        assert np.abs(m["u"][0][:, x] - ua).max() <= 1e-2 * ua.max()
+    assert np.abs(m["u"][1]).max() <= 1e-5 * ua.max()
+
+
 def test_rho0_is_inert():
     """rho_0 of Eq. 25 appears only in g_0, which enters neither u (c_0 = 0)
     nor p (Eq. N23 sums k >= 1): outputs are bit-identical."""
