@@ -1,0 +1,117 @@
+"""Planted mistakes: each case copies the oracle's C sources, makes one
+plausible mistake in the copy (a dropped term, a wrong sign, index or
+factor), builds it, and runs one of the pins against that build, which must
+fail. This shows that the pins which fix the oracle catch such a mistake.
+The committed oracle is never modified; the copies live in a temporary
+directory and run in a subprocess of their own."""
+import os
+import shutil
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+TESTS = os.path.join(ROOT, "tests")
+
+# (name, source file, text in it, planted replacement, pin module, pin, kwargs)
+MUTANTS = [
+    ("g_eq second-order term dropped (Eq. 25)", "lbm_oracle.c",
+     "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
+     "test_oracle_pins", "test_geq_moments_appendix_a1a", {}),
+    ("h_eq advective term sign (Eq. N25)", "lbm_oracle.c",
+     "W[k] * (CX[k] * phi * ux + CY[k] * phi * uy) / CS2;",
+     "W[k] * (CX[k] * phi * ux - CY[k] * phi * uy) / CS2;",
+     "test_oracle_pins", "test_ch_equilibrium_and_source_moments", {}),
+    ("G_k c.F term dropped (Eq. N20_1)", "lbm_oracle.c",
+     "G[k] = W[k] * (ugr + cF / CS2 + QT / (2.0 * CS2 * CS2));",
+     "G[k] = W[k] * (ugr + QT / (2.0 * CS2 * CS2));",
+     "test_oracle_pins", "test_force_distribution_moments_appendix_a1b", {}),
+    ("R_k prefactor sign (Eq. N26)", "lbm_oracle.c",
+     "R[k] = (1.0 - 1.0 / (2.0 * tau_i))", "R[k] = (1.0 + 1.0 / (2.0 * tau_i))",
+     "test_oracle_pins", "test_ch_equilibrium_and_source_moments", {}),
+    ("Laplacian centre weight (Eq. N31b)", "lbm_oracle.c",
+     "(z[nb(s, x, y, CX[k], CY[k])] - 2.0 * z[n] +",
+     "(z[nb(s, x, y, CX[k], CY[k])] - 1.0 * z[n] +",
+     "test_oracle_pins", "test_stencils_exact_on_quadratics", {"scheme": 0}),
+    ("gradient neighbour index transposed (Eq. N31a)", "lbm_oracle.c",
+     "d = (z[nb(s, x, y, CX[k], CY[k])] - z[nb(s, x, y, -CX[k], -CY[k])]) /",
+     "d = (z[nb(s, x, y, CX[k], CY[k])] - z[nb(s, x, y, -CY[k], -CX[k])]) /",
+     "test_oracle_pins", "test_stencils_exact_on_quadratics", {"scheme": 0}),
+    ("h_i(c) factor (rho_i + rho_N)/2 lost (Eq. N17)", "lbm_oracle.c",
+     "hf[i] = (p->rho_t[i] + p->rho_t[n]) / 2.0 * s;",
+     "hf[i] = (p->rho_t[i] + p->rho_t[n]) * s;",
+     "test_oracle_pins", "test_hfun_is_half_dH_dphi", {"N": 3}),
+    ("c -> phi inverse sign", "lbm_oracle.c",
+     "(p->rho_t[i] - p->rho_t[n])) /", "(p->rho_t[i] + p->rho_t[n])) /",
+     "test_oracle_pins", "test_fractions_definitions", {"N": 3}),
+    ("lambda right-hand side factor (Eq. N14)", "lbm_oracle.c",
+     "b[row] = 4.5 * p->eta * p->eta", "b[row] = 3.0 * p->eta * p->eta",
+     "test_oracle_pins", "test_lambda_golden_n3_equal_sigma", {}),
+    ("bounce-back keeps the direction (Section 4.2)", "lbm_oracle.c",
+     "*kk = OPP[k];", "*kk = k;",
+     "test_oracle_pins", "test_channel_flow_between_walls", {"tau_g": 0.8}),
+    ("D3Q15 g_eq second-order term dropped", "lbm_oracle3d.c",
+     "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
+     "test_oracle3d_pins", "test_geq3_moments", {}),
+    ("D3Q15 Laplacian centre weight", "lbm_oracle3d.c",
+     "- 2.0 * zf[q] +", "- 1.0 * zf[q] +",
+     "test_oracle3d_pins", "test_stencils3_exact_on_quadratics", {}),
+    ("D3Q15 streaming ignores z", "lbm_oracle3d.c",
+     "*q = nb(s, x, y, z, CX[k], CY[k], CZ[k]);", "*q = nb(s, x, y, z, CX[k], CY[k], 0);",
+     "test_oracle3d_pins", "test_flat_interface_along_z", {}),
+]
+
+_RUNNER = textwrap.dedent("""
+    import sys
+    sys.path[:0] = [{root!r}, {oracle!r}, {tests!r}]
+    import oracle
+    oracle._LIB_PATH = {lib!r}
+    oracle.build = lambda force=False: oracle._LIB_PATH
+    import importlib
+    pins = importlib.import_module({module!r})
+    try:
+        getattr(pins, {pin!r})(**{kwargs!r})
+    except AssertionError:
+        print("PIN FAILED")
+        sys.exit(3)
+    print("PIN PASSED")
+""")
+
+
+@pytest.mark.parametrize("name,src,old,new,module,pin,kwargs", MUTANTS,
+                         ids=[m[0] for m in MUTANTS])
+def test_pin_catches_planted_mistake(tmp_path, name, src, old, new, module, pin, kwargs):
+    text = open(os.path.join(ORACLE, src)).read()
+    assert text.count(old) == 1, f"planting site of '{name}' not found exactly once"
+    for f in ("lbm_oracle.c", "lbm_oracle3d.c"):
+        shutil.copy(os.path.join(ORACLE, f), tmp_path / f)
+    (tmp_path / src).write_text(text.replace(old, new))
+    lib = str(tmp_path / "liblbm_oracle_planted.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                    "-shared", "-o", lib, str(tmp_path / "lbm_oracle.c"),
+                    str(tmp_path / "lbm_oracle3d.c"), "-lm"], check=True)
+    code = _RUNNER.format(root=ROOT, oracle=ORACLE, tests=TESTS, lib=lib,
+                          module=module, pin=pin, kwargs=kwargs)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       timeout=600, env=dict(os.environ, OMP_NUM_THREADS="4"))
+    assert r.returncode == 3 and "PIN FAILED" in r.stdout, (name, r.returncode,
+                                                            r.stdout[-500:], r.stderr[-2000:])
+
+
+def test_unplanted_copy_passes(tmp_path):
+    """Control: the same harness on an unmodified copy passes the pins."""
+    for f in ("lbm_oracle.c", "lbm_oracle3d.c"):
+        shutil.copy(os.path.join(ORACLE, f), tmp_path / f)
+    lib = str(tmp_path / "liblbm_oracle_copy.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                    "-shared", "-o", lib, str(tmp_path / "lbm_oracle.c"),
+                    str(tmp_path / "lbm_oracle3d.c"), "-lm"], check=True)
+    for module, pin, kwargs in {(m[4], m[5], tuple(sorted(m[6].items()))) for m in MUTANTS}:
+        code = _RUNNER.format(root=ROOT, oracle=ORACLE, tests=TESTS, lib=lib,
+                              module=module, pin=pin, kwargs=dict(kwargs))
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           timeout=600, env=dict(os.environ, OMP_NUM_THREADS="4"))
+        assert r.returncode == 0 and "PIN PASSED" in r.stdout, (pin, r.stderr[-2000:])
