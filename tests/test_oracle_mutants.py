@@ -53,6 +53,20 @@ MUTANTS = [
     ("bounce-back keeps the direction (Section 4.2)", "lbm_oracle.c",
      "*kk = OPP[k];", "*kk = k;",
      "test_oracle_pins", "test_channel_flow_between_walls", {"tau_g": 0.8}),
+    ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
+     "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
+     "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
+     "test_oracle_pins", "test_stencils_exact_on_quadratics", {"scheme": 1}),
+    ("D3Q15 h_eq z term dropped", "lbm_oracle3d.c",
+     "CY[k] * phi * u[1] + CZ[k] * phi * u[2]) / CS2;", "CY[k] * phi * u[1]) / CS2;",
+     "test_oracle3d_pins", "test_ch3_moments", {}),
+    ("D3Q15 G_k c.F term dropped", "lbm_oracle3d.c",
+     "G[k] = W[k] * (ugr + cF / CS2 + QT / (2.0 * CS2 * CS2));",
+     "G[k] = W[k] * (ugr + QT / (2.0 * CS2 * CS2));",
+     "test_oracle3d_pins", "test_force_dist3_moments", {}),
+    ("D3Q15 R_k prefactor sign", "lbm_oracle3d.c",
+     "R[k] = (1.0 - 1.0 / (2.0 * tau_i))", "R[k] = (1.0 + 1.0 / (2.0 * tau_i))",
+     "test_oracle3d_pins", "test_ch3_moments", {}),
     ("D3Q15 g_eq second-order term dropped", "lbm_oracle3d.c",
      "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
      "test_oracle3d_pins", "test_geq3_moments", {}),
