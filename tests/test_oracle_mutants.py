@@ -53,6 +53,9 @@ MUTANTS = [
     ("bounce-back keeps the direction (Section 4.2)", "lbm_oracle.c",
      "*kk = OPP[k];", "*kk = k;",
      "test_oracle_pins", "test_channel_flow_between_walls", {"tau_g": 0.8}),
+    ("stencil ghost row below the wall wraps around", "lbm_oracle.c",
+     "if (yy < 0) yy = 0;", "if (yy < 0) yy += s->ny;",
+     "test_oracle_pins", "test_wall_ghost_rows_mirror_the_fluid", {"scheme": 0}),
     ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
      "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
      "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",

@@ -175,6 +175,32 @@ def test_stencils_exact_on_quadratics(scheme):
     s.close()
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_wall_ghost_rows_mirror_the_fluid(scheme):
+    """Walls: the stencils' ghost rows repeat the adjacent fluid row (zero
+    normal gradient, neutral wetting). That is a mirror about the wall planes
+    y = -1/2 and y = ny - 1/2, so on any field the wall stencils equal the
+    periodic stencils of the field extended by its mirror image to 2 ny rows,
+    bit for bit (same neighbour values, same order)."""
+    rng = np.random.default_rng(31 + scheme)
+    nx, ny = 12, 10
+    z = rng.uniform(-1, 1, (ny, nx))
+    sw = oracle.OracleSim(W.base_params(3, nx, ny, 1e-3, grad_scheme=scheme, wall_y=1))
+    sp = oracle.OracleSim(W.base_params(3, nx, 2 * ny, 1e-3, grad_scheme=scheme))
+    gw, lw = sw.stencils(z)
+    gp, lp = sp.stencils(np.concatenate([z, z[::-1]], axis=0))
+    if scheme == 0:
+        assert np.array_equal(gw, gp[:, :ny]) and np.array_equal(lw, lp[:ny])
+    else:
+        # Eq. N40 reaches two rows out: the second ghost row repeats the first
+        # fluid row as well (clamped), where the mirror gives the second; the
+        # rows two and more nodes from the wall still agree
+        assert np.array_equal(gw[:, 2:ny - 2], gp[:, 2:ny - 2])
+        assert np.array_equal(lw, lp[:ny])
+    sw.close()
+    sp.close()
+
+
 def test_central_gradient_sums_to_zero_periodic():
     """The central scheme is a difference of shifted copies: its global sum
     vanishes on a periodic grid (the global mass property noted after
