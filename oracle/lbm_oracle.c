@@ -641,6 +641,15 @@ void orc_chemical_potential(orc_state *s, double *C) {
   memcpy(C, s->C, sizeof(double) * (s->m.p.N - 1) * s->V);
 }
 
+/* J~ and grad(rho) (Eq. N18) of the current state, [2][y][x] each (for
+ * tests; reads only). */
+void orc_fluxes(orc_state *s, double *J, double *grho) {
+  zeroth_moment(s);
+  chemical_potentials(s);
+  memcpy(J, s->J, sizeof(double) * 2 * s->V);
+  memcpy(grho, s->grho, sizeof(double) * 2 * s->V);
+}
+
 /* Per-phase mass sum_x c_k, kinetic energy 1/2 sum rho |u|^2, max |u|,
  * summed serially in node order. */
 void orc_diagnostics(orc_state *s, double *mass, double *ke, double *umax) {

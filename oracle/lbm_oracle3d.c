@@ -481,6 +481,18 @@ void o3_moments(o3_state *s, double *phi, double *c, double *u, double *p, doubl
   if (rho) memcpy(rho, s->rho, sizeof(double) * V);
 }
 
+/* C_i, J~ and grad(rho) (Eq. N18) of the current state (for tests; reads
+ * only): C[N-1][V], J[3][V], grho[3][V]. */
+void o3_fluxes(o3_state *s, double *C, double *J, double *grho) {
+  int n = s->m.p.N - 1;
+  long V = s->V;
+  zeroth_moment(s);
+  chemical_potentials(s);
+  memcpy(C, s->C, sizeof(double) * n * V);
+  memcpy(J, s->J, sizeof(double) * 3 * V);
+  memcpy(grho, s->grho, sizeof(double) * 3 * V);
+}
+
 void o3_stencils(o3_state *s, const double *zf, double *grad, double *lap) {
   if (grad) gradient(s, zf, grad);
   if (lap) laplacian(s, zf, lap);

@@ -86,6 +86,7 @@ def _load():
         lib.orc_step.argtypes = [C.c_void_p, C.c_long]
         lib.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         lib.orc_chemical_potential.argtypes = [C.c_void_p, dp]
+        lib.orc_fluxes.argtypes = [C.c_void_p, dp, dp]
         lib.orc_diagnostics.argtypes = [C.c_void_p, dp, dp, dp]
         lib.orc_constants.argtypes = [C.c_void_p, dp, dp, dp, dp]
         lib.orc_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp]
@@ -112,6 +113,7 @@ def _load():
         lib.o3_step.argtypes = [C.c_void_p, C.c_long]
         lib.o3_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         lib.o3_stencils.argtypes = [C.c_void_p, dp, dp, dp]
+        lib.o3_fluxes.argtypes = [C.c_void_p, dp, dp, dp]
         lib.o3_geq.argtypes = [C.c_double] * 3 + [dp, dp]
         lib.o3_force_dist.argtypes = [C.c_double, dp, dp, dp, dp, dp]
         lib.o3_heq.argtypes = [C.c_double] * 3 + [dp, dp]
@@ -252,6 +254,13 @@ class OracleSim:
         C_ = np.zeros((self.N - 1, self.ny, self.nx))
         self.lib.orc_chemical_potential(self.h, _dp(C_))
         return C_
+
+    def fluxes(self):
+        """J~ and grad(rho) of Eq. N18 at the current state, [2][y][x] each."""
+        J = np.zeros((2, self.ny, self.nx))
+        grho = np.zeros((2, self.ny, self.nx))
+        self.lib.orc_fluxes(self.h, _dp(J), _dp(grho))
+        return J, grho
 
     def diagnostics(self):
         mass = np.zeros(self.N)
@@ -407,6 +416,15 @@ class OracleSim3D:
                "u": np.zeros((3,) + sh), "p": np.zeros(sh), "rho": np.zeros(sh)}
         self.lib.o3_moments(self.h, *[_dp(out[k]) for k in ("phi", "c", "u", "p", "rho")])
         return out
+
+    def fluxes(self):
+        """C_i, J~ and grad(rho) (Eq. N18) at the current state."""
+        sh = self.shape
+        C_ = np.zeros((self.N - 1,) + sh)
+        J = np.zeros((3,) + sh)
+        grho = np.zeros((3,) + sh)
+        self.lib.o3_fluxes(self.h, _dp(C_), _dp(J), _dp(grho))
+        return C_, J, grho
 
     def stencils(self, z):
         z = np.ascontiguousarray(z, dtype=np.float64)

@@ -213,3 +213,32 @@ def test_rho0_is_inert3():
     for o in outs[1:]:
         for k in ("phi", "u", "p"):
             assert np.array_equal(o[k], outs[0][k])
+
+
+def test_mass_flux_and_density_gradient3():
+    """Eq. N18 on D3Q15 with unequal densities: grad(rho) is Eq. N31a applied
+    to the density field and J~ = -sum_i (d rho / d phi_i) m_i grad C_i, with
+    d rho / d phi_i read off the density field itself (rho is linear in the
+    phi_i, Eqs. N2, N12, N29: a least-squares fit over the grid) instead of
+    the oracle's coefficients."""
+    N = 3
+    w = W.random_smooth3(21, N, 10, 8, 9, rho=[3.0, 1.0, 7.5], amp_u=0.02)
+    s = oracle.OracleSim3D(w.params)
+    s.init(w.c0, w.u0)
+    s.step(3)
+    C, J, grho = s.fluxes()
+    m = s.moments()
+    A = np.column_stack([np.ones(m["rho"].size)] + [m["phi"][i].ravel() for i in range(N - 1)])
+    coef, *_ = np.linalg.lstsq(A, m["rho"].ravel(), rcond=None)
+    assert np.abs(A @ coef - m["rho"].ravel()).max() < 1e-12
+    drho = coef[1:]
+    g_field, _ = s.stencils(m["rho"])
+    assert np.abs(grho - g_field).max() <= 1e-11 * np.abs(g_field).max()
+    mob = np.asarray(w.params["mobility"], dtype=float)
+    Jexp = np.zeros_like(J)
+    for i in range(N - 1):
+        gC, _ = s.stencils(C[i])
+        Jexp -= drho[i] * mob[i] * gC
+    assert np.abs(J).max() > 0
+    assert np.abs(J - Jexp).max() <= 1e-8 * np.abs(Jexp).max()
+    s.close()

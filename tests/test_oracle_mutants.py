@@ -56,6 +56,17 @@ MUTANTS = [
     ("stencil ghost row below the wall wraps around", "lbm_oracle.c",
      "if (yy < 0) yy = 0;", "if (yy < 0) yy += s->ny;",
      "test_oracle_pins", "test_wall_ghost_rows_mirror_the_fluid", {"scheme": 0}),
+    ("J~ sign (Eq. N18)", "lbm_oracle.c",
+     "Jx -= m->kap[i] * m->p.mob[i] * s->gC[2 * i * V + q];",
+     "Jx += m->kap[i] * m->p.mob[i] * s->gC[2 * i * V + q];",
+     "test_oracle_pins", "test_mass_flux_and_density_gradient", {"N": 3}),
+    ("J~ without the mobility (Eq. N18)", "lbm_oracle.c",
+     "Jy -= m->kap[i] * m->p.mob[i] * s->gC[(2 * i + 1) * V + q];",
+     "Jy -= m->kap[i] * s->gC[(2 * i + 1) * V + q];",
+     "test_oracle_pins", "test_mass_flux_and_density_gradient", {"N": 3}),
+    ("grad(rho) coefficient dropped (Eq. N18)", "lbm_oracle.c",
+     "rx += m->kap[i] * s->gphi[2 * i * V + q];", "rx += s->gphi[2 * i * V + q];",
+     "test_oracle_pins", "test_mass_flux_and_density_gradient", {"N": 3}),
     ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
      "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
      "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
@@ -70,6 +81,10 @@ MUTANTS = [
     ("D3Q15 R_k prefactor sign", "lbm_oracle3d.c",
      "R[k] = (1.0 - 1.0 / (2.0 * tau_i))", "R[k] = (1.0 + 1.0 / (2.0 * tau_i))",
      "test_oracle3d_pins", "test_ch3_moments", {}),
+    ("D3Q15 J~ sign", "lbm_oracle3d.c",
+     "J -= m->kap[i] * m->p.mob[i] * s->gC[(3 * i + a) * V + q];",
+     "J += m->kap[i] * m->p.mob[i] * s->gC[(3 * i + a) * V + q];",
+     "test_oracle3d_pins", "test_mass_flux_and_density_gradient3", {}),
     ("D3Q15 g_eq second-order term dropped", "lbm_oracle3d.c",
      "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
      "test_oracle3d_pins", "test_geq3_moments", {}),

@@ -378,6 +378,42 @@ def test_channel_flow_between_walls(tau_g):
     assert np.abs(m["u"][1]).max() <= 1e-5 * ua.max()
 
 
+@pytest.mark.parametrize("N", [3, 4])
+def test_mass_flux_and_density_gradient(N):
+    """Eq. N18 with unequal densities: grad(rho) is the gradient of the
+    density field and J~ the density flux that the phases' diffusive fluxes
+    m_i grad C_i carry, J~ = -sum_i (d rho / d phi_i) m_i grad C_i. Checked
+    along paths independent of the oracle's coefficients: d rho / d phi_i by
+    central differences of its own rho(phi) map (Eqs. N2, N12, N29; the map is
+    linear), grad(rho) as Eq. N31a applied to the rho field, grad C_i as
+    Eq. N31a applied to the C_i field."""
+    rng = np.random.default_rng(50 + N)
+    rho_t = rng.uniform(0.5, 12.0, N)
+    w = W.random_smooth(60 + N, N, 16, 12, rho=list(rho_t), amp_u=0.02)
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0, w.u0)
+    s.step(5)
+    J, grho = s.fluxes()
+    m = s.moments()
+    C = s.chemical_potential()
+    phi0 = m["phi"][:, 3, 5]
+    drho = np.zeros(N - 1)
+    for i in range(N - 1):
+        e = np.zeros(N - 1)
+        e[i] = 1e-3
+        drho[i] = (s.local_fractions(phi0 + e)[1] - s.local_fractions(phi0 - e)[1]) / 2e-3
+    g_field, _ = s.stencils(m["rho"])
+    assert np.abs(grho - g_field).max() <= 1e-11 * np.abs(g_field).max()
+    mob = np.asarray(w.params["mobility"], dtype=float)
+    Jexp = np.zeros_like(J)
+    for i in range(N - 1):
+        gC, _ = s.stencils(C[i])
+        Jexp -= drho[i] * mob[i] * gC
+    assert np.abs(J).max() > 0
+    assert np.abs(J - Jexp).max() <= 1e-9 * np.abs(Jexp).max()
+    s.close()
+
+
 def test_rho0_is_inert():
     """rho_0 of Eq. 25 appears only in g_0, which enters neither u (c_0 = 0)
     nor p (Eq. N23 sums k >= 1): outputs are bit-identical."""
