@@ -67,6 +67,13 @@ MUTANTS = [
     ("grad(rho) coefficient dropped (Eq. N18)", "lbm_oracle.c",
      "rx += m->kap[i] * s->gphi[2 * i * V + q];", "rx += s->gphi[2 * i * V + q];",
      "test_oracle_pins", "test_mass_flux_and_density_gradient", {"N": 3}),
+    ("CH relaxation with tau_g instead of tau_i (Eq. N24)", "lbm_oracle.c",
+     "double hs = hk - (hk - heq[k]) / m->p.tau[i] + R[k];",
+     "double hs = hk - (hk - heq[k]) / tg + R[k];",
+     "test_oracle_pins", "test_linear_ch_relaxation_rate", {"tau": 1.3}),
+    ("pressure's u.grad(rho) weight (Eq. N23)", "lbm_oracle.c",
+     "(sg + 0.5 * ugr + r * s_k(0, ux, uy))", "(sg + 1.5 * ugr + r * s_k(0, ux, uy))",
+     "test_oracle_pins", "test_translating_interface_with_density_contrast", {}),
     ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
      "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
      "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
