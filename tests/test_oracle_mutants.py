@@ -74,6 +74,12 @@ MUTANTS = [
     ("pressure's u.grad(rho) weight (Eq. N23)", "lbm_oracle.c",
      "(sg + 0.5 * ugr + r * s_k(0, ux, uy))", "(sg + 1.5 * ugr + r * s_k(0, ux, uy))",
      "test_oracle_pins", "test_translating_interface_with_density_contrast", {}),
+    ("start without (phi u)_prev (reading 8)", "lbm_oracle.c",
+     "s->phi_prev[i * V + q] = s->phi[i * V + q];", "s->phi_prev[i * V + q] = 0.0;",
+     "test_oracle_pins", "test_uniform_flow_populations_are_stationary", {}),
+    ("start with u_prev = 0 (reading 8)", "lbm_oracle.c",
+     "s->u_prev[q] = ux;", "s->u_prev[q] = 0.0;",
+     "test_oracle_pins", "test_uniform_flow_populations_are_stationary", {}),
     ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
      "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
      "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",

@@ -469,6 +469,26 @@ def test_translating_interface_with_density_contrast():
     assert np.ptp(m["p"]) <= 2e-3
 
 
+def test_uniform_flow_populations_are_stationary():
+    """A uniform mixture moving at constant velocity is a fixed point of the
+    populations themselves, not only of the moments: with the start state of
+    reading 8 ((phi u)_prev = phi u0, so the source R_k of Eq. N26 vanishes
+    from the first step) every h and g after each step equals its value at
+    the start (to roundoff)."""
+    w = W.quiescent(3, 10, 6, frac=[0.2, 0.5, 0.3], rho=[1, 4, 2])
+    u0 = np.zeros((2, 6, 10))
+    u0[0], u0[1] = 0.03, -0.02
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0, u0)
+    st0 = s.get_state()
+    for _ in range(3):
+        s.step(1)
+        st = s.get_state()
+        for k in ("h", "g"):
+            assert np.abs(st[k] - st0[k]).max() <= 1e-15, k
+    s.close()
+
+
 def test_rho0_is_inert():
     """rho_0 of Eq. 25 appears only in g_0, which enters neither u (c_0 = 0)
     nor p (Eq. N23 sums k >= 1): outputs are bit-identical."""
