@@ -242,3 +242,57 @@ def test_mass_flux_and_density_gradient3():
     assert np.abs(J).max() > 0
     assert np.abs(J - Jexp).max() <= 1e-8 * np.abs(Jexp).max()
     s.close()
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_channel_flow_between_walls3(axis):
+    """Halfway bounce-back walls in y on D3Q15: a uniform mixture driven by
+    a body force rho g along x or z settles on the plane Poiseuille parabola
+    u(y) = g (y + 1/2)(ny - 1/2 - y) / (2 nu), nu = (tau_g - 1/2)/3 (Eq.
+    N21_1), within 1%, with no flow in the other directions."""
+    nx, ny, nz, g, tau_g = 4, 16, 4, 1e-6, 0.8
+    grav = [0.0, 0.0, 0.0]
+    grav[axis] = g
+    c = np.broadcast_to(np.array([0.2, 0.5, 0.3])[:, None, None, None],
+                        (3, nz, ny, nx)).copy()
+    p = W.base_params3(3, nx, ny, nz, 1e-3, wall_y=1, tau_g=tau_g, gravity=grav)
+    s = oracle.OracleSim3D(p)
+    s.init(c)
+    s.step(6000)
+    m = s.moments()
+    s.close()
+    nu = (tau_g - 0.5) / 3.0
+    y = np.arange(ny) + 0.5
+    ua = g * y * (ny - y) / (2.0 * nu)
+    prof = m["u"][axis][:, :, :]
+    for z in range(nz):
+        for x in range(nx):
+            assert np.abs(prof[z, :, x] - ua).max() <= 1e-2 * ua.max()
+    for a in range(3):
+        if a != axis:
+            assert np.abs(m["u"][a]).max() <= 1e-5 * ua.max()
+
+
+def test_translating_interface_with_density_contrast3():
+    """Galilean invariance on D3Q15: two flat interfaces normal to z between
+    pure phases of densities 3 and 1, carried by a uniform flow U along z,
+    keep u = U within 3% and p uniform to 2e-3 after 200 steps (the
+    u . grad(rho) terms of Eqs. N23 and N20_1 are active)."""
+    import math
+    nx, ny, nz, U = 4, 4, 64, 0.01
+    eta = 2 * math.sqrt(2)
+    band = W._layer(nz, 1, nz / 4, 3 * nz / 4, eta)[:, 0]
+    c = np.zeros((2, nz, ny, nx))
+    c[0] = band[:, None, None]
+    c[1] = 1 - c[0]
+    u0 = np.zeros((3, nz, ny, nx))
+    u0[2] = U
+    p = W.base_params3(2, nx, ny, nz, 1e-3, rho=[3.0, 1.0], eta=eta)
+    s = oracle.OracleSim3D(p)
+    s.init(c, u0)
+    s.step(200)
+    m = s.moments()
+    s.close()
+    assert np.abs(m["u"][2] - U).max() <= 0.03 * U
+    assert np.abs(m["u"][:2]).max() <= 1e-6 * U
+    assert np.ptp(m["p"]) <= 2e-3

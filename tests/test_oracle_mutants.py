@@ -98,6 +98,15 @@ MUTANTS = [
      "J -= m->kap[i] * m->p.mob[i] * s->gC[(3 * i + a) * V + q];",
      "J += m->kap[i] * m->p.mob[i] * s->gC[(3 * i + a) * V + q];",
      "test_oracle3d_pins", "test_mass_flux_and_density_gradient3", {}),
+    ("D3Q15 pressure's u.grad(rho) weight", "lbm_oracle3d.c",
+     "(sg + 0.5 * ugr + r * s_k(0, u))", "(sg + 1.5 * ugr + r * s_k(0, u))",
+     "test_oracle3d_pins", "test_translating_interface_with_density_contrast3", {}),
+    ("D3Q15 gravity dropped", "lbm_oracle3d.c",
+     "F[a] = r * m->p.grav[a];", "F[a] = 0.0;",
+     "test_oracle3d_pins", "test_channel_flow_between_walls3", {"axis": 0}),
+    ("D3Q15 bounce-back keeps the direction", "lbm_oracle3d.c",
+     "*kk = opp(k);", "*kk = k;",
+     "test_oracle3d_pins", "test_channel_flow_between_walls3", {"axis": 2}),
     ("D3Q15 g_eq second-order term dropped", "lbm_oracle3d.c",
      "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
      "test_oracle3d_pins", "test_geq3_moments", {}),
