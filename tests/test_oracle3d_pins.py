@@ -296,3 +296,56 @@ def test_translating_interface_with_density_contrast3():
     assert np.abs(m["u"][2] - U).max() <= 0.03 * U
     assert np.abs(m["u"][:2]).max() <= 1e-6 * U
     assert np.ptp(m["p"]) <= 2e-3
+
+
+def test_laplace_law_cylinder3():
+    """A drop column along z (a cylinder of radius R in a two-plane D3Q15
+    box) carries the 2-D pressure jump sigma / R (Section 4.1): within 5% at
+    W = 4, R = 10 after 4000 steps (0.969 when this pin was written)."""
+    n, R, sig, nz = 48, 10.0, 1e-3, 2
+    d2 = W.drop(n, n, n / 2, n / 2, R)
+    c = np.zeros((2, nz, n, n))
+    c[1] = d2[None]
+    c[0] = 1 - c[1]
+    s = oracle.OracleSim3D(W.base_params3(2, n, n, nz, sig))
+    s.init(c)
+    s.step(4000)
+    m = s.moments()
+    s.close()
+    y, x = np.mgrid[0:n, 0:n]
+    r = np.hypot(x - n / 2, y - n / 2)
+    p0 = m["p"][0]
+    dp = p0[r < R / 2].mean() - p0[(m["c"][0][0] > 0.999) & (r > R + 10)].mean()
+    assert abs(dp / (sig / R) - 1) < 0.05, dp / (sig / R)
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.3])
+def test_linear_ch_relaxation_rate3(tau):
+    """On D3Q15, a small cosine mode along z of a uniform binary mixture at
+    phi0 = 0.8 decays at the linearised Cahn-Hilliard rate
+    m K^2 (beta^2/eta^2 h'(phi0) + lambda K^2), h'(phi0) = -(1 - 3 phi0^2)/4
+    (N = 2, unit densities), with lambda and beta from the D2Q9 oracle's
+    setup of the same parameters (Eqs. N14, N36) and K^2 from the D3Q15
+    Laplacian (Eq. N31b): within 10% whatever tau_i."""
+    nx, ny, nz, phi0, eps, M, T = 2, 2, 16, 0.8, 1e-5, 0.1, 3000
+    z = np.arange(nz)
+    mode = np.cos(2 * np.pi * z / nz)
+    p2 = W.base_params(2, 4, 4, 1e-2, tau=tau, tau_g=0.8, mobility=M)
+    s2 = oracle.OracleSim(p2)
+    k = s2.constants()
+    s2.close()
+    lam = float(np.ravel(k["lam"])[0])
+    bulk = k["beta"] ** 2 / p2["eta"] ** 2
+    c1 = np.broadcast_to(((1 + phi0 + eps * mode) / 2)[:, None, None], (nz, ny, nx))
+    s = oracle.OracleSim3D(W.base_params3(2, nx, ny, nz, 1e-2, tau=tau, tau_g=0.8,
+                                          mobility=M))
+    _, lap = s.stencils(np.broadcast_to(mode[:, None, None], (nz, ny, nx)))
+    K2 = -lap[0, 0, 0]
+    rate = M * K2 * (bulk * (-(1 - 3 * phi0 ** 2) / 4) + lam * K2)
+    s.init(np.stack([c1, 1 - c1]))
+    s.step(T)
+    ph = s.moments()["phi"][0][:, 0, 0]
+    s.close()
+    amp = 2 * np.mean((ph - ph.mean()) * mode)
+    measured = -np.log(amp / eps) / T
+    assert abs(measured / rate - 1) < 0.1, (measured, rate)

@@ -107,6 +107,13 @@ MUTANTS = [
     ("D3Q15 bounce-back keeps the direction", "lbm_oracle3d.c",
      "*kk = opp(k);", "*kk = k;",
      "test_oracle3d_pins", "test_channel_flow_between_walls3", {"axis": 2}),
+    ("D3Q15 CH relaxation with tau_g", "lbm_oracle3d.c",
+     "hk - (hk - heq[k]) / m->p.tau[i] + R[k];", "hk - (hk - heq[k]) / tg + R[k];",
+     "test_oracle3d_pins", "test_linear_ch_relaxation_rate3", {"tau": 1.3}),
+    ("D3Q15 surface force sign", "lbm_oracle3d.c",
+     "for (int i = 0; i < n; ++i) F[a] += s->C[i * V + q] * s->gphi[(3 * i + a) * V + q];",
+     "for (int i = 0; i < n; ++i) F[a] -= s->C[i * V + q] * s->gphi[(3 * i + a) * V + q];",
+     "test_oracle3d_pins", "test_laplace_law_cylinder3", {}),
     ("D3Q15 g_eq second-order term dropped", "lbm_oracle3d.c",
      "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
      "test_oracle3d_pins", "test_geq3_moments", {}),
