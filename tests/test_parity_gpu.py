@@ -224,10 +224,8 @@ def test_precision_forms_error(prec):
     assert np.abs(gd[0] / od[0] - 1).max() <= 1e-6
 
 
-# max |dphi|, max |du| / max |u|, centre-of-mass shift (nodes) allowed
-# after 2000 steps of the 512x512 collision; every form meets the 1e-3
-# target on phi (measured 3.4e-4, 8.3e-4, 3.2e-4).
-# (max |dphi|, max |du| / max |u|, drop centres in nodes); measured
+# Allowed after 2000 steps of the 512x512 collision: (max |dphi|,
+# max |du| / max |u|, shift of the drop centres in nodes); measured
 # FP32 3.4e-4 / 1.8e-4, FP16 3.3e-4 / 1.8e-4, BF16 3.4e-4 / 1.9e-4
 COLLISION_BOUNDS = {"fp32": (1e-3, 1e-3, 1e-2), "fp16": (1e-3, 1e-3, 1e-2),
                     "bf16": (1e-3, 1e-3, 5e-2)}
