@@ -80,6 +80,9 @@ MUTANTS = [
     ("start with u_prev = 0 (reading 8)", "lbm_oracle.c",
      "s->u_prev[q] = ux;", "s->u_prev[q] = 0.0;",
      "test_oracle_pins", "test_uniform_flow_populations_are_stationary", {}),
+    ("kinetic energy without the 1/2", "lbm_oracle.c",
+     "e += 0.5 * s->rho[q] * u2;", "e += s->rho[q] * u2;",
+     "test_oracle_pins", "test_diagnostics_of_known_states", {}),
     ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
      "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
      "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",

@@ -489,6 +489,26 @@ def test_uniform_flow_populations_are_stationary():
     s.close()
 
 
+def test_diagnostics_of_known_states():
+    """The diagnostics (per-phase mass sum_x c_k, kinetic energy
+    1/2 sum_x rho |u|^2, max |u|) on states whose values are known in closed
+    form: a uniform mixture with densities 1, 4, 2 and fractions 0.2, 0.5,
+    0.3 moving at U = (0.03, -0.02) on 10 x 6 nodes has mass 60 c_k, rho =
+    sum_k rho~_k c_k = 2.8, KE = 1/2 60 rho |U|^2 and max |u| = |U|."""
+    frac, rho_t = np.array([0.2, 0.5, 0.3]), np.array([1.0, 4.0, 2.0])
+    w = W.quiescent(3, 10, 6, frac=list(frac), rho=list(rho_t))
+    u0 = np.zeros((2, 6, 10))
+    u0[0], u0[1] = 0.03, -0.02
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0, u0)
+    mass, ke, umax = s.diagnostics()
+    s.close()
+    U2 = 0.03 ** 2 + 0.02 ** 2
+    np.testing.assert_allclose(mass, 60 * frac, rtol=1e-13)
+    assert abs(ke - 0.5 * 60 * (rho_t @ frac) * U2) <= 1e-13 * ke
+    assert abs(umax - math.sqrt(U2)) <= 1e-15
+
+
 def test_rho0_is_inert():
     """rho_0 of Eq. 25 appears only in g_0, which enters neither u (c_0 = 0)
     nor p (Eq. N23 sums k >= 1): outputs are bit-identical."""
