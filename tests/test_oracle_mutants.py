@@ -83,6 +83,13 @@ MUTANTS = [
     ("kinetic energy without the 1/2", "lbm_oracle.c",
      "e += 0.5 * s->rho[q] * u2;", "e += s->rho[q] * u2;",
      "test_oracle_pins", "test_diagnostics_of_known_states", {}),
+    ("a_i of Eq. N30 with tau_i - 1/4", "lbm_oracle.c",
+     "m->a[i] = p->mob[i] / (CS2 * (p->tau[i] - 0.5));",
+     "m->a[i] = p->mob[i] / (CS2 * (p->tau[i] - 0.25));",
+     "test_oracle_pins", "test_linear_ch_relaxation_rate", {"tau": 1.0}),
+    ("beta of Eq. N36 with 2 sqrt 2", "lbm_oracle.c",
+     "return sqrt(3.0 * sqrt(2.0) * smin * p->eta);", "return sqrt(2.0 * sqrt(2.0) * smin * p->eta);",
+     "test_oracle_pins", "test_surface_tension_integral", {}),
     ("mixed gradient upwind weight (Eq. N40)", "lbm_oracle.c",
      "5.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
      "4.0 * z[nb(s, x, y, CX[k], CY[k])] - 3.0 * z[n] -",
