@@ -481,6 +481,14 @@ void o3_moments(o3_state *s, double *phi, double *c, double *u, double *p, doubl
   if (rho) memcpy(rho, s->rho, sizeof(double) * V);
 }
 
+/* The populations h[N-1][15][V] and g[15][V] of the current state (for
+ * tests; reads only). */
+void o3_populations(const o3_state *s, double *h, double *g) {
+  long V = s->V;
+  memcpy(h, s->h, sizeof(double) * (s->m.p.N - 1) * O3_Q * V);
+  memcpy(g, s->g, sizeof(double) * O3_Q * V);
+}
+
 /* C_i, J~ and grad(rho) (Eq. N18) of the current state (for tests; reads
  * only): C[N-1][V], J[3][V], grho[3][V]. */
 void o3_fluxes(o3_state *s, double *C, double *J, double *grho) {

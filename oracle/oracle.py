@@ -114,6 +114,7 @@ def _load():
         lib.o3_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         lib.o3_stencils.argtypes = [C.c_void_p, dp, dp, dp]
         lib.o3_fluxes.argtypes = [C.c_void_p, dp, dp, dp]
+        lib.o3_populations.argtypes = [C.c_void_p, dp, dp]
         lib.o3_geq.argtypes = [C.c_double] * 3 + [dp, dp]
         lib.o3_force_dist.argtypes = [C.c_double, dp, dp, dp, dp, dp]
         lib.o3_heq.argtypes = [C.c_double] * 3 + [dp, dp]
@@ -416,6 +417,14 @@ class OracleSim3D:
                "u": np.zeros((3,) + sh), "p": np.zeros(sh), "rho": np.zeros(sh)}
         self.lib.o3_moments(self.h, *[_dp(out[k]) for k in ("phi", "c", "u", "p", "rho")])
         return out
+
+    def populations(self):
+        """h[N-1][15] and g[15] of the current state."""
+        sh = self.shape
+        h = np.zeros((self.N - 1, 15) + sh)
+        g = np.zeros((15,) + sh)
+        self.lib.o3_populations(self.h, _dp(h), _dp(g))
+        return h, g
 
     def fluxes(self):
         """C_i, J~ and grad(rho) (Eq. N18) at the current state."""

@@ -349,3 +349,23 @@ def test_linear_ch_relaxation_rate3(tau):
     amp = 2 * np.mean((ph - ph.mean()) * mode)
     measured = -np.log(amp / eps) / T
     assert abs(measured / rate - 1) < 0.1, (measured, rate)
+
+
+def test_uniform_flow3_populations_are_stationary():
+    """On D3Q15 too a uniform moving mixture is a fixed point of the
+    populations from the start state of reading 8 ((phi u)_prev = phi u0, so
+    R_k of Eq. N26 vanishes from the first step): h and g after each step
+    equal their start values (to roundoff)."""
+    N, sh = 3, (5, 6, 7)
+    c = np.broadcast_to(np.array([0.2, 0.5, 0.3])[:, None, None, None], (N,) + sh).copy()
+    u0 = np.zeros((3,) + sh)
+    u0[0], u0[1], u0[2] = 0.03, -0.02, 0.015
+    s = oracle.OracleSim3D(W.base_params3(N, sh[2], sh[1], sh[0], 1e-3, rho=[1.0, 4.0, 2.0]))
+    s.init(c, u0)
+    h0, g0 = s.populations()
+    for _ in range(3):
+        s.step(1)
+        h, g = s.populations()
+        assert np.abs(h - h0).max() <= 1e-15
+        assert np.abs(g - g0).max() <= 1e-15
+    s.close()

@@ -124,6 +124,9 @@ MUTANTS = [
      "for (int i = 0; i < n; ++i) F[a] += s->C[i * V + q] * s->gphi[(3 * i + a) * V + q];",
      "for (int i = 0; i < n; ++i) F[a] -= s->C[i * V + q] * s->gphi[(3 * i + a) * V + q];",
      "test_oracle3d_pins", "test_laplace_law_cylinder3", {}),
+    ("D3Q15 start without (phi u)_prev (reading 8)", "lbm_oracle3d.c",
+     "s->phi_prev[i * V + q] = s->phi[i * V + q];", "s->phi_prev[i * V + q] = 0.0;",
+     "test_oracle3d_pins", "test_uniform_flow3_populations_are_stationary", {}),
     ("D3Q15 g_eq second-order term dropped", "lbm_oracle3d.c",
      "cu * cu / (2.0 * CS2 * CS2)", "0.0 * cu",
      "test_oracle3d_pins", "test_geq3_moments", {}),
