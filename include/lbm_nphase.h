@@ -166,8 +166,9 @@ lbm_status lbm_nphase_diagnostics(lbm_nphase_t *h, double *mass, double *ke,
  * the reduced values) is a 1 MiB static device array inside the library,
  * which every GPU that loads the library holds until the process exits.
  * The paper has no counterpart; this is a library convenience.
- *  - Limit: at most 16384 tiles of 32 x 8 nodes (e.g. 2048 x 2048); larger
- *    grids return LBM_EINVAL.
+ *  - Limit: at most 16384 partial sums, one per tile of the grid: tiles of
+ *    32 x 8 nodes on D2Q9 (e.g. 2048 x 2048) and of 32 x 4 x 2 nodes on
+ *    D3Q15 (e.g. 128 x 128 x 256). Larger grids return LBM_EINVAL.
  *  - The handle's device must be current. The first call on a device looks
  *    up the array's device address; make that first call before any stream
  *    capture.
@@ -268,7 +269,8 @@ lbm_status lbm_nphase_batch_destroy(lbm_nphase_batch_t *b);
  * phi(t-1), u(t-1) and a 64-byte header with N, nx, ny, precision and the
  * step count) as one blob of lbm_nphase_state_bytes() bytes, in host or
  * device memory. lbm_nphase_set_state accepts a blob of a handle with the
- * same N, grid and precision (else LBM_EINVAL) and leaves the handle
+ * same N, grid, lattice, precision, walls and gradient scheme (else
+ * LBM_EINVAL) and leaves the handle
  * initialised at that state; continuing from it reproduces the uninterrupted
  * run bit for bit. Both synchronise. Not part of the paper. */
 size_t lbm_nphase_state_bytes(const lbm_nphase_t *h);

@@ -701,7 +701,8 @@ lbm_status lbm_nphase_set_state(lbm_nphase_t *h, const void *src, size_t bytes) 
   if (memcmp(hd.magic, "LBMNPHS2", 8) != 0 || hd.N != h->prm.N ||
       hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.nz != depth(&h->prm) ||
       hd.lattice != h->prm.lattice ||
-      hd.precision != h->prm.precision ||
+      hd.precision != h->prm.precision || hd.wall_y != h->prm.wall_y ||
+      hd.grad_scheme != h->prm.grad_scheme ||
       hd.payload != lbm_nphase_state_bytes(h) - sizeof(hd))
     return LBM_EINVAL;
   h->cur = 0;
@@ -893,6 +894,10 @@ extern "C" lbm_status lbm_nphase_diagnostics_static(lbm_nphase_t *h,
     for (int k = 0; k < N; ++k) mass[k] = r[k];
   if (ke) *ke = r[N];
   if (umax) *umax = r[N + 1];
+  // A bounded device wait that gave up (in a step kernel or here) is
+  // reported before the finite check, as lbm_nphase_diagnostics does.
+  const lbm_status es = check_err(h);
+  if (es != LBM_OK) return es;
   if (!ok) {
     h->unstable = true;
     return LBM_EUNSTABLE;

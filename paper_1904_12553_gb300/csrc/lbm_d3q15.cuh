@@ -953,57 +953,66 @@ __global__ void init3_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
   }
 }
 
+// Equilibrium start in FP64 for every storage form (as init_pop_kernel in
+// two dimensions): phi, its Laplacian, C_i, h^eq and g^eq in double with the
+// constants `d`, each stored value rounded once into its form.
 template <int P, int NP, bool WALL>
-__global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
+__global__ void init3_pop_kernel(const KArgs3<P> A, const KArgs<LBM_FP64> d,
+                                 const double *__restrict__ cin,
+                                 const double *__restrict__ uin, double p0,
+                                 double r0, double r1, double r2, double r3,
+                                 double r4) {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
   const KArgs<P> &a = A.a;
+  const double rt[5] = {r0, r1, r2, r3, r4};
   const int nx = a.nx, ny = a.ny, nz = A.nz;
   const size_t V = a.V;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < V;
        q += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(q % nx), y = (int)((q / nx) % ny), z = (int)(q / ((size_t)nx * ny));
-    T ph[NP], lp[NP];
+    double ph[NP], lp[NP];
     for (int i = 0; i < NP; ++i) {
-      const T *f = a.pp_out + (size_t)i * V;
-      T s[27];
+      double s[27];
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx)
-            s[((dz + 1) * 3 + dy + 1) * 3 + dx + 1] = f[node3<WALL>(x + dx, y + dy, z + dz, nx, ny, nz)];
-      T gtmp[3];
+            s[((dz + 1) * 3 + dy + 1) * 3 + dx + 1] =
+                phi_of_c<NP>(cin, V, node3<WALL>(x + dx, y + dy, z + dz, nx, ny, nz), i, rt);
+      double gtmp[3];
       ph[i] = s[13];
-      stencil3<T, 3, 3>(s, 1, 1, 1, gtmp, lp[i]);
+      stencil3<double, 3, 3>(s, 1, 1, 1, gtmp, lp[i]);
     }
-    T cc[NP + 1], rho, hf[NP];
-    local_algebra<P, NP>(a, ph, cc, rho, hf);
-    const T u[3] = {a.u_out[q], a.u_out[V + q], a.u_out[2 * V + q]};
-    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const T p0 = (T)p0d;
-    if constexpr (Prec<P>::REF) a.u_out[3 * V + q] = p0;
+    double cc[NP + 1], rho, hf[NP];
+    local_algebra<LBM_FP64, NP>(d, ph, cc, rho, hf);
+    double u[3];
+    for (int e = 0; e < 3; ++e) u[e] = uin ? uin[(size_t)e * V + q] : 0.0;
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    if constexpr (Prec<P>::REF) a.u_out[3 * V + q] = (T)p0;
     for (int k = 1; k < 15; ++k) {
-      const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
-      const T geq = w3_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+      const double cu = c3x(k) * u[0] + c3y(k) * u[1] + c3z(k) * u[2];
+      const double geq =
+          w3_of<double>(k) * (3.0 * p0 + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
       if constexpr (Prec<P>::MIX) {
         const size_t qs = source3<WALL>(x, y, z, k, nx, ny, nz);
         const T sux = a.u_out[qs], suy = a.u_out[V + qs], suz = a.u_out[2 * V + qs];
-        a.gm_out[(size_t)(k - 1) * V + q] = to_S<Sm>(
-            geq * (a.sg_st / w3_of<T>(k)) -
-            // every source starts at p0 (stored as its p(t-1) above)
-            (Prec<P>::REF ? g_ref3p(cdotu3(k, sux, suy, suz), sux, suy, suz, p0,
-                                    a.rho_base * a.sg_st, T(3) * a.sg_st)
-                          : T(0)));
+        // every source starts at p0 (stored as its p(t-1) above)
+        const T ref = Prec<P>::REF ? g_ref3p(cdotu3(k, sux, suy, suz), sux, suy, suz,
+                                             (T)p0, a.rho_base * a.sg_st, T(3) * a.sg_st)
+                                   : T(0);
+        a.gm_out[(size_t)(k - 1) * V + q] =
+            store_once<Sm>(geq * (d.sg_st / w3_of<double>(k)) - (double)ref);
       } else
-        a.gm_out[(size_t)(k - 1) * V + q] = geq;
+        a.gm_out[(size_t)(k - 1) * V + q] = store_once<Sm>(geq);
     }
     for (int i = 0; i < NP; ++i) {
-      T Ci = a.bulk * hf[i];
-      for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
-      const T aC = a.a[i] * Ci;
-      T moving = T(0);
+      double Ci = d.bulk * hf[i];
+      for (int j = 0; j < NP; ++j) Ci -= d.lam[i][j] * lp[j];
+      const double aC = d.a[i] * Ci;
+      double moving = 0.0;  // sum of the moving populations as stored
       for (int k = 1; k < 15; ++k) {
-        const T cu = T(c3x(k)) * u[0] + T(c3y(k)) * u[1] + T(c3z(k)) * u[2];
-        const T heq = w3_of<T>(k) * (aC + T(3) * ph[i] * cu);
+        const double cu = c3x(k) * u[0] + c3y(k) * u[1] + c3z(k) * u[2];
+        const double heq = w3_of<double>(k) * (aC + 3.0 * ph[i] * cu);
         if constexpr (Prec<P>::MIX) {
           const size_t qs = source3<WALL>(x, y, z, k, nx, ny, nz);
           const T ref =
@@ -1011,18 +1020,20 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, double p0d) {
                   ? adv_units(cdotu3(k, a.u_out[qs], a.u_out[V + qs], a.u_out[2 * V + qs]),
                               a.pp_out[(size_t)i * V + qs], T(3) * a.sh_st)
                   : T(0);
-          const Sm sv = to_S<Sm>(heq * (a.sh_st / w3_of<T>(k)) - ref);
+          const Sm sv = store_once<Sm>(heq * (d.sh_st / w3_of<double>(k)) - (double)ref);
           a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = sv;
-          moving = __fmaf_rn(w3_of<T>(k) * a.sh_ld, __fadd_rn(to_T(sv), ref), moving);
+          moving += (double)(w3_of<T>(k) * a.sh_ld) * (double)__fadd_rn(to_T(sv), ref);
         } else {
-          a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = heq;
-          moving = __fadd_rn_T(moving, heq);
+          const Sm hv = store_once<Sm>(heq);
+          a.hm_out[((size_t)(i * 14 + k - 1)) * V + q] = hv;
+          moving += (double)hv;
         }
       }
       if constexpr (P == LBM_FP64)
-        a.h0_out[(size_t)i * V + q] = ph[i] + (w3_of<T>(0) - T(1)) * aC;
+        a.h0_out[(size_t)i * V + q] = ph[i] + (w3_of<double>(0) - 1.0) * aC;
       else
-        a.h0_out[(size_t)i * V + q] = -moving;
+        a.h0_out[(size_t)i * V + q] =
+            store_once<T>((ph[i] - (double)a.pp_out[(size_t)i * V + q]) - moving);
     }
   }
 }
@@ -1164,10 +1175,13 @@ cudaError_t launch_init3_np(const Consts &c, const Grid &g, int cur,
       A.a, cin, uin, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const KArgs<LBM_FP64> d = make_args<LBM_FP64>(c, g, cur ^ 1, MODE_STEP, Outputs{});
   if (wall)
-    init3_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(A, p0);
+    init3_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(
+        A, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   else
-    init3_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(A, p0);
+    init3_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(
+        A, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   return cudaGetLastError();
 }
 

@@ -1238,10 +1238,54 @@ __global__ void init_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
   }
 }
 
+// Store an FP64 value in a storage type with one rounding (to nearest, ties
+// to even). The 16-bit types go through FP32 rounded to odd (truncate, then
+// set the last bit if anything was cut off), which keeps the second rounding
+// exact: Boldo and Melquiond, "Emulation of FMA and correctly rounded sums:
+// proved algorithms using rounding to odd" (IEEE Trans. Computers, 2008),
+// for a target of at most 22 significant bits.
+template <typename S> __device__ __forceinline__ S store_once(double v);
+template <> __device__ __forceinline__ double store_once(double v) { return v; }
+template <> __device__ __forceinline__ float store_once(double v) {
+  return __double2float_rn(v);
+}
+__device__ __forceinline__ float float_round_odd(double v) {
+  const float t = __double2float_rz(v);
+  return (double)t == v ? t : __uint_as_float(__float_as_uint(t) | 1u);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 store_once(double v) {
+  return to_S<__nv_bfloat16>(float_round_odd(v));
+}
+template <> __device__ __forceinline__ __half store_once(double v) {
+  return to_S<__half>(float_round_odd(v));
+}
+
+// Order parameter phi_i of node q from the volume fractions (inverse of
+// Eqs. N2 and N12), in FP64.
+template <int NP>
+__device__ __forceinline__ double phi_of_c(const double *__restrict__ c,
+                                           size_t V, size_t q, int i,
+                                           const double *rt) {
+  const double rN = rt[NP];
+  return (2.0 * (rt[i] * c[(size_t)i * V + q] - rN * c[(size_t)NP * V + q]) -
+          (rt[i] - rN)) /
+         (rt[i] + rN);
+}
+
+// Equilibrium start in FP64 for every storage form: phi and its Laplacian
+// from the volume fractions, C_i (Eqs. N17, N18), h^eq (Eq. N25) and g^eq
+// (Eq. 25) are computed in double with the constants `d`, and each stored
+// value is rounded once into its form. The 16-bit references (and the FP32
+// phi(t-1), u(t-1) they use) are those the step kernel decodes with.
 template <int P, int NP, bool WALL>
-__global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
+__global__ void init_pop_kernel(const KArgs<P> a, const KArgs<LBM_FP64> d,
+                                const double *__restrict__ cin,
+                                const double *__restrict__ uin, double p0,
+                                double r0, double r1, double r2, double r3,
+                                double r4) {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
+  const double rt[5] = {r0, r1, r2, r3, r4};
   const int nx = a.nx, ny = a.ny;
   const size_t V = a.V;
   T *h0 = a.h0_out;
@@ -1250,70 +1294,75 @@ __global__ void init_pop_kernel(const KArgs<P> a, double p0d) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < V;
        q += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(q % nx), y = (int)(q / nx);
-    T ph[NP], lp[NP];
+    double ph[NP], lp[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      const T *f = a.pp_out + (size_t)i * V;
-      T s[9];
+      double s[9];
 #pragma unroll
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx)
-          s[(dy + 1) * 3 + dx + 1] =
-              f[(size_t)wrap_y<WALL>(y + dy, ny) * nx + wrap(x + dx, nx)];
+          s[(dy + 1) * 3 + dx + 1] = phi_of_c<NP>(
+              cin, V, (size_t)wrap_y<WALL>(y + dy, ny) * nx + wrap(x + dx, nx), i, rt);
       ph[i] = s[4];
-      lp[i] = laplacian<T, 3>(s, 1, 1);
+      lp[i] = laplacian<double, 3>(s, 1, 1);
     }
-    T cc[NP + 1], rho, hf[NP];
-    local_algebra<P, NP>(a, ph, cc, rho, hf);
-    const T ux = a.u_out[q], uy = a.u_out[V + q];
-    const T uu = ux * ux + uy * uy;
-    const T p0 = (T)p0d;
-    if constexpr (Prec<P>::REF) a.u_out[2 * V + q] = p0;
+    double cc[NP + 1], rho, hf[NP];
+    local_algebra<LBM_FP64, NP>(d, ph, cc, rho, hf);
+    const double ux = uin ? uin[q] : 0.0, uy = uin ? uin[V + q] : 0.0;
+    const double uu = ux * ux + uy * uy;
+    if constexpr (Prec<P>::REF) a.u_out[2 * V + q] = (T)p0;
 #pragma unroll
     for (int k = 1; k < 9; ++k) {
-      const T cu = T(cx_of(k)) * ux + T(cy_of(k)) * uy;
-      const T geq = w_of<T>(k) * (T(3) * p0 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+      const double cu = cx_of(k) * ux + cy_of(k) * uy;
+      const double geq =
+          w_of<double>(k) * (3.0 * p0 + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
       if constexpr (Prec<P>::MIX) {
         const size_t qs = source_node<WALL>(x, y, k, nx, ny);
         const T sux = a.u_out[qs], suy = a.u_out[V + qs];
-        // every source starts at p0 (stored as its p(t-1) below)
-        const T ref = Prec<P>::REF ? g_refp(cdotu(k, sux, suy), sux, suy, p0,
+        // every source starts at p0 (stored as its p(t-1) above)
+        const T ref = Prec<P>::REF ? g_refp(cdotu(k, sux, suy), sux, suy, (T)p0,
                                             a.rho_base * a.sg_st, T(3) * a.sg_st)
                                    : T(0);
-        gm[(size_t)(k - 1) * V + q] = to_S<Sm>(geq * (a.sg_st / w_of<T>(k)) - ref);
+        gm[(size_t)(k - 1) * V + q] =
+            store_once<Sm>(geq * (d.sg_st / w_of<double>(k)) - (double)ref);
       } else
-        gm[(size_t)(k - 1) * V + q] = geq;
+        gm[(size_t)(k - 1) * V + q] = store_once<Sm>(geq);
     }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      T Ci = a.bulk * hf[i];
+      double Ci = d.bulk * hf[i];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) Ci -= a.lam[i][j] * lp[j];
-      const T aC = a.a[i] * Ci;
-      T moving = T(0);
+      for (int j = 0; j < NP; ++j) Ci -= d.lam[i][j] * lp[j];
+      const double aC = d.a[i] * Ci;
+      double moving = 0.0;  // sum of the moving populations as stored
 #pragma unroll
       for (int k = 1; k < 9; ++k) {
-        const T heq = w_of<T>(k) * (aC + T(3) * ph[i] * (T(cx_of(k)) * ux + T(cy_of(k)) * uy));
+        const double heq =
+            w_of<double>(k) * (aC + 3.0 * ph[i] * (cx_of(k) * ux + cy_of(k) * uy));
         if constexpr (Prec<P>::MIX) {
           const size_t qs = source_node<WALL>(x, y, k, nx, ny);
           const T ref = Prec<P>::REF ? adv_units(cdotu(k, a.u_out[qs], a.u_out[V + qs]),
                                                  a.pp_out[(size_t)i * V + qs], T(3) * a.sh_st)
                                      : T(0);
-          const Sm sv = to_S<Sm>(heq * (a.sh_st / w_of<T>(k)) - ref);
+          const Sm sv = store_once<Sm>(heq * (d.sh_st / w_of<double>(k)) - (double)ref);
           hm[((size_t)(i * 8 + k - 1)) * V + q] = sv;
-          moving = __fadd_rn(moving, __fmul_rn(Prec<P>::REF ? __fadd_rn(to_T(sv), ref) : to_T(sv),
-                                               w_of<T>(k) * a.sh_ld));
+          const T dec = Prec<P>::REF ? __fadd_rn(to_T(sv), ref) : to_T(sv);
+          moving += (double)(w_of<T>(k) * a.sh_ld) * (double)dec;
         } else {
-          hm[((size_t)(i * 8 + k - 1)) * V + q] = heq;
-          moving = __fadd_rn_T(moving, heq);
+          const Sm hv = store_once<Sm>(heq);
+          hm[((size_t)(i * 8 + k - 1)) * V + q] = hv;
+          moving += (double)hv;
         }
       }
-      // FP64: h_0 = h_0^eq. Other forms: d_0 = h_0^eq - phi = -sum_{k>=1} h_k^eq.
+      // FP64: h_0 = h_0^eq. Other forms: d_0 = h_0 - phi(t-1) with phi(t-1)
+      // the stored (rounded) phi, so that phi(t-1) + d_0 + sum_{k>=1} h_k is
+      // phi up to the rounding of d_0.
       if constexpr (P == LBM_FP64)
-        h0[(size_t)i * V + q] = ph[i] + (w_of<T>(0) - T(1)) * aC;
+        h0[(size_t)i * V + q] = ph[i] + (w_of<double>(0) - 1.0) * aC;
       else
-        h0[(size_t)i * V + q] = -moving;
+        h0[(size_t)i * V + q] =
+            store_once<T>((ph[i] - (double)a.pp_out[(size_t)i * V + q]) - moving);
     }
   }
 }
@@ -1436,10 +1485,13 @@ cudaError_t launch_init_np(const Consts &c, const Grid &g, int cur,
       a, cin, uin, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const KArgs<LBM_FP64> d = make_args<LBM_FP64>(c, g, cur ^ 1, MODE_STEP, Outputs{});
   if (wall)
-    init_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(a, p0);
+    init_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(
+        a, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   else
-    init_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(a, p0);
+    init_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(
+        a, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   return cudaGetLastError();
 }
 

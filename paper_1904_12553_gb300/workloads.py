@@ -163,6 +163,29 @@ def static_drops(nx=128, ny=128, R=20.0, centres=((40, 64), (88, 64)), N=3,
     return Workload(f"static_drops_N{N}_{nx}x{ny}", p, c, None, 0.0, steps)
 
 
+def paper_static_drops(N=3, absent=None, nx=300, ny=100, R=20.0,
+                       precision="fp64", eta=ETA_W4, steps=20000) -> Workload:
+    """The paper's static drops (Section 4.1, Eqs. N31_a, N31_b): drops of
+    phases 1..N-1 (R = 20) at (50, 50), (150, 50), (250, 50) in phase N, a
+    300 x 100 periodic box; densities 20:1:5 (N = 3) or 20:1:10:5 (N = 4),
+    all sigma = 0.01, tau = 0.8, m = 0.001, eta = sqrt(2), beta = sqrt(0.06).
+
+    ``absent`` (a 0-based phase index) sets that phase's fraction to zero
+    everywhere and leaves its drop out: the paper's reduction-consistency
+    case is N = 4 with the third phase absent, against N = 3."""
+    rho = {3: [20.0, 1.0, 5.0], 4: [20.0, 1.0, 10.0, 5.0]}[N]
+    centres = ((50.0, 50.0), (150.0, 50.0), (250.0, 50.0))
+    c = np.zeros((N, ny, nx))
+    for j in range(N - 1):
+        if j != absent:
+            c[j] = drop(nx, ny, centres[j][0], centres[j][1], R, eta)
+    c[N - 1] = 1.0 - c[:N - 1].sum(0)
+    p = base_params(N, nx, ny, 0.01, rho=rho, tau=0.8, mobility=0.001,
+                    precision=precision, eta=eta, beta=math.sqrt(0.06))
+    tag = "" if absent is None else f"_absent{absent + 1}"
+    return Workload(f"paper_static_drops_N{N}{tag}", p, c, None, 0.0, steps)
+
+
 def lens(nx=256, ny=256, R=40.0, s13=0.8e-3, s12=1e-3, s23=None,
          tau=0.8, mobility=0.1, rho=None, precision="fp32", steps=20000,
          eta=ETA_W4, wall_y=1, N=3, beta=0.0) -> Workload:
@@ -192,6 +215,55 @@ def lens(nx=256, ny=256, R=40.0, s13=0.8e-3, s12=1e-3, s23=None,
     p = base_params(N, nx, ny, sig, rho=rho, tau=tau, mobility=mobility,
                     precision=precision, eta=eta, wall_y=wall_y, beta=beta)
     return Workload(f"lens_{nx}x{ny}_s13_{s13:g}", p, c, None, 0.0, steps)
+
+
+# Tension ratios sigma_12 : sigma_13 : sigma_23 of the paper's lens runs
+# (Section 4.2, Tables 1 and 2).
+PAPER_LENS_RATIOS = {
+    "1:4/3:1": (1.0, 4.0 / 3.0, 1.0),
+    "1:1:1": (1.0, 1.0, 1.0),
+    "0.6:0.6:1": (0.6, 0.6, 1.0),
+}
+
+
+def paper_lens(ratio="1:1:1", scale="min", n=150, R=30.0,
+               rho=(10.0, 1.0, 5.0), precision="fp64", eta=ETA_W4,
+               beta=math.sqrt(0.06), steps=200000) -> Workload:
+    """The paper's own liquid lens (Section 4.2, Eq. N35): a drop of phase 1
+    (R = 30) centred on the flat interface between phase 2 above and phase 3
+    below, in a 150 x 150 box periodic in x with halfway bounce-back walls in
+    y; densities 10:1:5, tau_g = tau_i = 0.8, m_i = 0.1, eta = sqrt(2),
+    beta = sqrt(0.06).
+
+    The paper gives the tensions only as ratios. ``scale="min"`` makes the
+    smallest tension 0.01, the value for which Eq. N36 gives the stated
+    beta = sqrt(0.06) at eta = sqrt(2) (as in the static-drop runs of
+    Section 4.1); ``scale="unit"`` takes the ratio's 1 as 0.01 (for 0.6:0.6:1
+    this puts sigma_min at 0.006, where Eq. N36 would give beta^2 = 0.036).
+    A number sets the scale itself.
+    """
+    r12, r13, r23 = PAPER_LENS_RATIOS[ratio]
+    if scale == "min":
+        unit = 0.01 / min(r12, r13, r23)
+    elif scale == "unit":
+        unit = 0.01
+    else:
+        unit = float(scale)
+    N = 3
+    xc, yc = (n - 1) / 2.0, (n - 1) / 2.0
+    c = np.zeros((N, n, n))
+    c[0] = drop(n, n, xc, yc, R, eta, px=True, py=False)
+    _, y = _grid(n, n)
+    c[1] = np.maximum(_step(y - yc, eta) - c[0], 0.0)
+    c[2] = 1.0 - c[0] - c[1]
+    sig = np.zeros((N, N))
+    sig[0, 1] = sig[1, 0] = r12 * unit
+    sig[0, 2] = sig[2, 0] = r13 * unit
+    sig[1, 2] = sig[2, 1] = r23 * unit
+    p = base_params(N, n, n, sig, rho=list(rho), tau=0.8, mobility=0.1,
+                    precision=precision, eta=eta, wall_y=1,
+                    beta=0.0 if beta is None else beta)
+    return Workload(f"paper_lens_{ratio}_{n}", p, c, None, 0.0, steps)
 
 
 def puddle(g, nx=400, ny=200, R=30.0, sigma=0.01, rho=(3.0, 1.0, 6.0),

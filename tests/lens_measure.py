@@ -60,6 +60,61 @@ def measure(c_below, c_drop, far_cols=8):
     return d, top - y_ref, y_ref - bot, y_ref
 
 
+def contour_points(c, lvl=0.5):
+    """Points where the field c crosses lvl along the grid edges (rows and
+    columns, linear interpolation), as an array of (x, y)."""
+    pts = []
+    a, b = c[:, :-1], c[:, 1:]
+    yy, xx = np.nonzero((a - lvl) * (b - lvl) < 0)
+    t = (lvl - a[yy, xx]) / (b[yy, xx] - a[yy, xx])
+    pts.append(np.stack([xx + t, yy.astype(float)], 1))
+    a, b = c[:-1, :], c[1:, :]
+    yy, xx = np.nonzero((a - lvl) * (b - lvl) < 0)
+    t = (lvl - a[yy, xx]) / (b[yy, xx] - a[yy, xx])
+    pts.append(np.stack([xx.astype(float), yy + t], 1))
+    return np.concatenate(pts)
+
+
+def fit_circle(p):
+    """Least-squares circle x^2 + y^2 = 2 a x + 2 b y + k through points p;
+    returns (a, b, r)."""
+    A = np.stack([2 * p[:, 0], 2 * p[:, 1], np.ones(len(p))], 1)
+    rhs = (p * p).sum(1)
+    (a, b, k), *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    return a, b, math.sqrt(k + a * a + b * b)
+
+
+def measure_fit(c_below, c_drop, far_cols=8, margin=0.25):
+    """Lens length and cap heights from circles fitted to the two caps.
+
+    The c_drop = 1/2 contour points above and below the far-field level of
+    the lower fluid (leaving out a band of margin x the cap height around it,
+    where the diffuse triple junction rounds the tips) are fitted with one
+    circle each; the caps' circles meet at the triple junctions, d is their
+    distance and h_1, h_2 the caps' heights above and below that chord.
+    Returns d, h_up, h_down, y_chord."""
+    d0, hu0, hd0, y_ref = measure(c_below, c_drop, far_cols)
+    pts = contour_points(c_drop)
+    up = pts[pts[:, 1] > y_ref + max(2.0, margin * hu0)]
+    dn = pts[pts[:, 1] < y_ref - max(2.0, margin * hd0)]
+    a1, b1, r1 = fit_circle(up)
+    a2, b2, r2 = fit_circle(dn)
+    # intersections of the two circles
+    dx, dy = a2 - a1, b2 - b1
+    L = math.hypot(dx, dy)
+    t = (r1 * r1 - r2 * r2 + L * L) / (2 * L)
+    hh = math.sqrt(max(r1 * r1 - t * t, 0.0))
+    mx, my = a1 + t * dx / L, b1 + t * dy / L
+    d = 2.0 * hh
+    # unit normal of the chord pointing to the upper cap
+    nx_, ny_ = dx / L, dy / L
+    if ny_ < 0:
+        nx_, ny_ = -nx_, -ny_
+    h_up = r1 + ((a1 - mx) * nx_ + (b1 - my) * ny_)
+    h_down = r2 - ((a2 - mx) * nx_ + (b2 - my) * ny_)
+    return d, h_up, h_down, my
+
+
 def angles(d, h_up, h_down):
     return (math.degrees(2 * math.atan(2 * h_up / d)),
             math.degrees(2 * math.atan(2 * h_down / d)))
@@ -68,6 +123,44 @@ def angles(d, h_up, h_down):
 def neumann_symmetric(s12, s):
     """Cap angle of a symmetric lens (sigma_13 = sigma_23 = s), Eq. N32."""
     return math.degrees(math.acos(s12 / (2 * s)))
+
+
+def neumann(s12, s13, s23):
+    """Contact angles (theta_1, theta_2) in degrees of a lens of phase 1
+    between phase 2 (theta_1 side) and phase 3 (theta_2 side), Eq. N32."""
+    t1 = math.acos((s12 ** 2 + s23 ** 2 - s13 ** 2) / (2 * s12 * s23))
+    t2 = math.acos((s13 ** 2 + s23 ** 2 - s12 ** 2) / (2 * s13 * s23))
+    return math.degrees(t1), math.degrees(t2)
+
+
+def lens_from_area(A, t1_deg, t2_deg):
+    """Length d and cap heights (h_1, h_2) of a lens of area A whose caps
+    meet the flat interface at theta_1, theta_2: Eq. N33 solved for d, then
+    Eq. N34."""
+    th = [math.radians(t1_deg), math.radians(t2_deg)]
+    k = sum((t / math.sin(t) - math.cos(t)) / math.sin(t) for t in th)
+    d = 2.0 * math.sqrt(A / k)
+    h = [0.5 * d * (1 - math.cos(t)) / math.sin(t) for t in th]
+    return d, h[0], h[1]
+
+
+def contour_area(c_drop, lvl=0.5):
+    """Area inside the c_drop = lvl contour: per column, the distance
+    between the lowest and highest crossing (linear interpolation)."""
+    ny, nx = c_drop.shape
+    area = 0.0
+    for x in range(nx):
+        col = c_drop[:, x]
+        idx = np.where(col > lvl)[0]
+        if len(idx) == 0:
+            continue
+        ymax, ymin = idx.max(), idx.min()
+        top = ymax + (_cross(col[ymax], col[ymax + 1], lvl)
+                      if ymax + 1 < ny else 0.5)
+        bot = ymin - 1 + (_cross(col[ymin - 1], col[ymin], lvl)
+                          if ymin >= 1 else 0.5)
+        area += top - bot
+    return area
 
 
 def de_gennes_thickness(g, spread, rho1, rho2, rho3, upper=True):

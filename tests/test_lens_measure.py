@@ -1,0 +1,106 @@
+"""CPU checks of the lens measurement helpers (Section 4.2).
+
+The lens geometry of Eqs. N32-N34 is checked against its own definition:
+two circular caps on a chord of length d meeting the chord at theta_1 and
+theta_2. A diffuse lens is drawn from the exact signed distance to that
+shape and the measurement must give d, h_1, h_2, the angles and the area
+back; Eq. N32 is checked on the symmetric case and on the triangle of
+forces it encodes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lens_measure as LM
+
+
+def _caps(d, t1, t2, xc, yref):
+    """Circles (centre y, radius) of the upper and lower caps."""
+    a1, a2 = math.radians(t1), math.radians(t2)
+    r1, r2 = d / (2 * math.sin(a1)), d / (2 * math.sin(a2))
+    return (yref - r1 * math.cos(a1), r1), (yref + r2 * math.cos(a2), r2)
+
+
+def _diffuse_lens(nx, ny, d, t1, t2, xc, yref, eta=math.sqrt(2.0)):
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float),
+                       indexing="ij")
+    (cy1, r1), (cy2, r2) = _caps(d, t1, t2, xc, yref)
+    sd = np.maximum(np.hypot(x - xc, y - cy1) - r1,
+                    np.hypot(x - xc, y - cy2) - r2)
+    step = lambda v: 0.5 + 0.5 * np.tanh(v / (math.sqrt(2.0) * eta))  # noqa
+    c_drop = step(-sd)
+    c_below = step(yref - y) * (1.0 - c_drop)
+    return c_below, c_drop
+
+
+def _exact_area(d, t1, t2):
+    area = 0.0
+    for t in (math.radians(t1), math.radians(t2)):
+        r = d / (2 * math.sin(t))
+        area += r * r * (t - math.sin(t) * math.cos(t))   # circular segment
+    return area
+
+
+@pytest.mark.parametrize("d,t1,t2", [(80.0, 60.0, 60.0), (110.0, 34.0, 34.0),
+                                     (74.0, 83.6, 48.2), (60.0, 45.0, 70.0)])
+def test_measure_recovers_a_drawn_lens(d, t1, t2):
+    nx, ny, xc, yref = 160, 150, 79.5, 74.3
+    c_below, c_drop = _diffuse_lens(nx, ny, d, t1, t2, xc, yref)
+    h1 = d / 2 * math.tan(math.radians(t1) / 2)
+    h2 = d / 2 * math.tan(math.radians(t2) / 2)
+    # contour crossing on the far-field line: the heights are exact, d is
+    # short by the rounding of the kinked tip between two rows (up to
+    # ~(1/tan t1 + 1/tan t2)/2 nodes)
+    dm, hu, hd, y_ref = LM.measure(c_below, c_drop)
+    assert abs(y_ref - yref) < 0.02
+    assert abs(hu - h1) < 0.05 and abs(hd - h2) < 0.05
+    kink = 0.5 * (1 / math.tan(math.radians(t1)) + 1 / math.tan(math.radians(t2)))
+    assert -kink - 0.1 < dm - d < 0.1
+    # circles fitted to the caps: d, h and the angles
+    dm, hu, hd, y_chord = LM.measure_fit(c_below, c_drop)
+    assert abs(y_chord - yref) < 0.02
+    assert abs(dm - d) < 0.05
+    assert abs(hu - h1) < 0.05 and abs(hd - h2) < 0.05
+    a1, a2 = LM.angles(dm, hu, hd)
+    assert abs(a1 - t1) < 0.1 and abs(a2 - t2) < 0.1
+    area = _exact_area(d, t1, t2)
+    assert abs(LM.contour_area(c_drop) / area - 1) < 5e-3
+    # Eqs. N33/N34 from the exact area and angles give the drawn shape back
+    dd, g1, g2 = LM.lens_from_area(area, t1, t2)
+    assert abs(dd - d) < 1e-9 * d
+    assert abs(g1 - h1) < 1e-9 * d and abs(g2 - h2) < 1e-9 * d
+
+
+def test_neumann_angles():
+    """Eq. N32: the symmetric closed form, the values behind Table 2, and
+    the force triangle (unit tensions along the three interfaces sum to
+    zero)."""
+    for s in (0.6e-3, 0.8e-3, 1.0e-3):
+        t1, t2 = LM.neumann(s, s, 1e-3)
+        assert abs(t1 - LM.neumann_symmetric(1e-3, s)) < 1e-12
+        assert abs(t1 - t2) < 1e-12
+    t1, t2 = LM.neumann(1.0, 4.0 / 3.0, 1.0)
+    assert abs(t1 - 83.62) < 0.01 and abs(t2 - 48.19) < 0.01
+    assert abs(LM.neumann(1, 1, 1)[0] - 60.0) < 1e-12
+    for s12, s13, s23 in ((1.0, 4.0 / 3.0, 1.0), (0.6, 0.6, 1.0),
+                          (0.7, 1.1, 1.3)):
+        t1, t2 = (math.radians(v) for v in LM.neumann(s12, s13, s23))
+        # flat interface along -x from the junction, the 1|2 cap above at
+        # theta_1 over +x, the 1|3 cap below at theta_2
+        f = (s23 * np.array([-1.0, 0.0]) +
+             s12 * np.array([math.cos(t1), math.sin(t1)]) +
+             s13 * np.array([math.cos(t2), -math.sin(t2)]))
+        assert np.abs(f).max() < 1e-12
+
+
+def test_paper_table2_analytic_lengths_follow_eqs_n33_n34():
+    """Table 2's analytic d, h_1, h_2 are consistent with Eq. N34 at the
+    Eq. N32 angles (the table's theta_2 = 52.5 of the 1:4/3:1 row is not)."""
+    for (s12, s13, s23), (d, h1, h2) in (
+            ((1.0, 4.0 / 3.0, 1.0), (73.8, 33.0, 16.5)),
+            ((1.0, 1.0, 1.0), (80.7, 23.3, 23.3)),
+            ((0.6, 0.6, 1.0), (113.9, 17.2, 17.2))):
+        t1, t2 = LM.neumann(s12, s13, s23)
+        assert abs(d / 2 * math.tan(math.radians(t1) / 2) - h1) < 0.06
+        assert abs(d / 2 * math.tan(math.radians(t2) / 2) - h2) < 0.06

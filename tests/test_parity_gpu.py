@@ -177,6 +177,21 @@ def test_lens_walls_fp64_1000_steps():
     compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
 
 
+@pytest.mark.parametrize("s13", [0.6e-3, 0.8e-3, 1.0e-3])
+def test_lens_256_fp64_1000_steps_full_size(s13):
+    """The liquid lens at its full size (N=3, 256x256, R=40, walls in y,
+    sigma_12 = 1e-3, sigma_13 = sigma_23 = s13) against the oracle."""
+    w = W.lens(nx=256, ny=256, R=40, s13=s13, precision="fp64")
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
+def test_collision_512_fp64_1000_steps_full_size():
+    """The N=4 drop collision at its full size (512x512, seeded sigma and
+    tau, drops moving at 0.01) against the oracle."""
+    w = W.collision(seed=3, n=512, precision="fp64", accept=_accept(4))
+    compare(gpu_run(w, 1000), oracle_run(w, 1000), 1e-10, 1e-12)
+
+
 def test_collision_n4_fp64_1000_steps():
     """N=4 drop collision with initial velocities, seeded sigma and tau,
     reduced to 128x128."""

@@ -65,6 +65,46 @@ def test_static_diagnostics_match_workspace_diagnostics(prec):
     s2.close()
 
 
+def test_static_diagnostics_d3q15_handle():
+    """A D3Q15 handle: one partial per 32 x 4 x 2 tile in the same array."""
+    from paper_1904_12553_gb300 import Solver, binding, workloads as W
+    w = W.random_smooth3(23, 3, 34, 9, 6, amp_u=0.02, precision="fp32")
+    s = Solver(w.params)
+    s.init(w.c0, w.u0)
+    for _ in range(2):
+        s.step(4)
+        ref = binding.lbm_nphase_diagnostics(s.handle, s.N)
+        got = binding.lbm_nphase_diagnostics_static(s.handle, s.N)
+        np.testing.assert_allclose(got[0], ref[0], rtol=1e-12)
+        assert abs(got[1] - ref[1]) <= 1e-12 * abs(ref[1])
+        assert abs(got[2] - ref[2]) <= 1e-12 * abs(ref[2])
+    s.close()
+
+
+def test_static_diagnostics_reports_a_wait_that_gave_up():
+    """After a bounded device wait gave up (the library's self-test waits on
+    a barrier nothing signals; no fault), the static entry point reports
+    LBM_ETIMEOUT like the workspace one, and the handle refuses to step."""
+    from paper_1904_12553_gb300 import LbmError, Solver, binding, workloads as W
+    w = W.random_smooth(24, 3, 64, 40, precision="fp32", amp_u=0.01)
+    s = Solver(w.params)
+    s.init(w.c0, w.u0)
+    s.step(2)
+    binding.lbm_nphase_selftest_wait_timeout(s.handle)
+    with pytest.raises(LbmError) as e:
+        binding.lbm_nphase_diagnostics_static(s.handle, s.N)
+    assert e.value.status == 4          # LBM_ETIMEOUT
+    with pytest.raises(LbmError) as e:
+        s.step(1)
+    assert e.value.status == 6          # LBM_ESTATE
+    s.init(w.c0, w.u0)
+    s.step(2)
+    ref = binding.lbm_nphase_diagnostics(s.handle, s.N)
+    got = binding.lbm_nphase_diagnostics_static(s.handle, s.N)
+    np.testing.assert_allclose(got[0], ref[0], rtol=1e-12)
+    s.close()
+
+
 def test_static_diagnostics_rejects_grids_beyond_limit():
     from paper_1904_12553_gb300 import LbmError, Solver, binding, workloads as W
     # 8192 x 520 nodes = 256 x 65 tiles > 16384 partial slots
