@@ -83,6 +83,10 @@ def traffic_from_profiles(kernel_tag: str):
     return None
 
 
+# Wall-clock windows of the timed GPU loops of this run, for the clocks record.
+GPU_WINDOWS: list = []
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while alive."""
 
@@ -113,19 +117,26 @@ class ClockSampler:
     def mark(self, t0, t1):
         self.window = (t0, t1)
 
-    def stop(self):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
-                    "samples": 0}
-        t0, t1 = self.window or (0, 1e30)
-        sel = [s for (t, s) in self.samples if t0 - 0.05 <= t <= t1 + 0.05]
-        sel = sel or [s for (_, s) in self.samples]
+    def summary_windows(self, wins):
+        """summary() over the union of several (t0, t1) windows."""
+        keep = []
+        for (t, line) in list(self.samples):
+            for (a, b) in wins:
+                if a is None or a - 0.05 <= t <= b + 0.05:
+                    keep.append((t, line))
+                    break
+        saved, self.samples = self.samples, keep
+        try:
+            return self.summary()
+        finally:
+            self.samples = saved
+
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, max clock and throttle reasons of the samples
+        taken between t0 and t1 (all samples if None)."""
+        t0 = -1e30 if t0 is None else t0
+        t1 = 1e30 if t1 is None else t1
+        sel = [s for (t, s) in list(self.samples) if t0 - 0.05 <= t <= t1 + 0.05]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
@@ -141,7 +152,33 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sel)}
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        # The headline's timed region can be a few milliseconds (one
+        # sample at most), so the record covers the whole GPU run that
+        # holds it: the forms' warm-up and timed steps back to back. The
+        # samples inside the headline's own timed window are counted too.
+        wins = GPU_WINDOWS or [(None, None)]
+        out = self.summary_windows(wins)
+        out["window"] = ("the timed loops of every form of this run (the "
+                         "headline, the other storage forms, the ensemble, "
+                         "D3Q15)")
+        if self.window:
+            inner = self.summary(*self.window)
+            out["timed_window"] = {"samples": inner["samples"],
+                                   "sm_mhz": inner["sm_mhz"],
+                                   "reasons": inner["reasons"]}
+        return out
 
 
 def accept_sigma(N=None):
@@ -209,6 +246,7 @@ def time_form(w, prec, steps, warmup, dist=None, segments=None):
         ev[i + 1].record(s.stream)
     torch.cuda.synchronize()
     wall1 = time.time()
+    GPU_WINDOWS.append((wall0, wall1))
     ms = ev[0].elapsed_time(ev[-1])
     if segments is not None and nseg > 1:
         segments.extend((ev[i].elapsed_time(ev[i + 1]), bounds[i + 1] - bounds[i])
@@ -268,11 +306,13 @@ def d3q15_run(n=256, steps=100, prec="fp32"):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
     e0.record(s.stream)
     for _ in range(steps):
         s.step(1)
     e1.record(s.stream)
     torch.cuda.synchronize()
+    GPU_WINDOWS.append((wall0, time.time()))
     ms = e0.elapsed_time(e1) / steps
     s.close()
     N, V = 3, w.V
@@ -309,10 +349,12 @@ def batch_run(steps=50, ncases=256):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
     e0.record(b.stream)
     b.step(steps)
     e1.record(b.stream)
     torch.cuda.synchronize()
+    GPU_WINDOWS.append((wall0, time.time()))
     ms_b = e0.elapsed_time(e1)
     sched = b.schedule()
     b.close()
@@ -420,7 +462,6 @@ def run_ours(args, dist, rank, world):
                                                args.warmup, dist, segs)
     if sampler:
         sampler.mark(wa, wb)
-    clocks = sampler.stop() if sampler else None
     ms_step = ms / args.steps
     value = replica_value(world, V, args.steps, ms)
     if rank != 0:
@@ -429,6 +470,7 @@ def run_ours(args, dist, rank, world):
     B = alg_bytes_per_node(N, "fp32")
     achieved = B * V / (ms_step / 1e3) / 1e9
     if args.kernel_only:
+        clocks = sampler.stop() if sampler else None
         print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS",
                           "n_gpus": world, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": ms_step,
@@ -462,6 +504,7 @@ def run_ours(args, dist, rank, world):
         for prec3 in ("fp32", "bf16", "fp16"):
             forms["d3q15_" + prec3] = d3q15_run(prec=prec3)
     e2e_v, h2d, d2h = e2e_run(w, "fp32", args.steps)
+    clocks = sampler.stop() if sampler else None
     cpu = cpu_baseline() if (world == 1 and not args.quick) else None
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -479,8 +522,10 @@ def run_ours(args, dist, rank, world):
                      "peak_kind": peak_kind,
                      "alg_bytes_per_node": B,
                      "traffic": traffic_from_profiles("tile_kernel_tma_fp32_n5_2048")},
+        # through the C ABI from pinned host memory: init (H2D), the same
+        # K steps, moments (D2H); at small K the init and read-back dominate
         "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": args.steps},
         "gpu_launches": args.steps,
         "segments": segment_summary(segs, V),
         # the same rate counted per LB equation (N per node update)

@@ -479,6 +479,22 @@ def flat_interface(N=3, nx=8, ny=64, sigma=1e-3, tau=0.8, mobility=0.1,
     return Workload(f"flat_N{N}_{nx}x{ny}", p, c, None, 0.0, steps)
 
 
+def pair_band(sigma, k, l, rho=None, nx=4, ny=64, beta=0.0, eta=ETA_W4,
+              tau=0.8, mobility=0.1, precision="fp64",
+              steps=10000) -> Workload:
+    """A band of phase k (ny/4 <= y < 3ny/4) in phase l, periodic in y, the
+    other phases absent: two flat k|l interfaces. ``sigma`` is the NxN
+    tension matrix of the whole system (0-based k, l)."""
+    sig = np.array(sigma, dtype=np.float64)
+    N = sig.shape[0]
+    c = np.zeros((N, ny, nx))
+    c[k] = _layer(ny, nx, ny / 4.0, 3.0 * ny / 4.0, eta)
+    c[l] = 1.0 - c[k]
+    p = base_params(N, nx, ny, sig, rho=rho, tau=tau, mobility=mobility,
+                    precision=precision, eta=eta, beta=beta)
+    return Workload(f"pair_band_{k + 1}{l + 1}_N{N}", p, c, None, 0.0, steps)
+
+
 def quiescent(N=3, nx=16, ny=12, frac=None, precision="fp64", steps=1000,
               sigma=1e-3, rho=None, wall_y=0) -> Workload:
     """Spatially uniform mixture at rest."""

@@ -163,6 +163,20 @@ def contour_area(c_drop, lvl=0.5):
     return area
 
 
+def band_tension(phi, c, lam, beta, eta):
+    """Tension of each of the two flat interfaces of a relaxed band (fields
+    [.][ny] along y, periodic): the excess of the discrete free energy whose
+    variation gives the step's chemical potential (Eqs. N11, N17, N18, N31b
+    in one dimension): 1/2 sum_ij lambda_ij dphi_i dphi_j with forward
+    differences (their variation is the three-point Laplacian) plus
+    beta^2/(2 eta^2) sum_k c_k^2 (1 - c_k)^2 (Eq. N17 is half of the
+    derivative of the printed sum), divided by two."""
+    dphi = np.roll(phi, -1, axis=1) - phi
+    grad = 0.5 * np.einsum("ij,iy,jy->y", lam, dphi, dphi)
+    bulk = beta * beta / (2 * eta * eta) * (c * c * (1 - c) ** 2).sum(0)
+    return float((grad + bulk).sum() / 2)
+
+
 def de_gennes_thickness(g, spread, rho1, rho2, rho3, upper=True):
     """Asymptotic thickness of a puddle of fluid 1 floating between fluid 2
     above and fluid 3 below, with spread = s12 + s13 - s23 > 0 (Eq. N37).

@@ -104,3 +104,70 @@ def test_paper_table2_analytic_lengths_follow_eqs_n33_n34():
         t1, t2 = LM.neumann(s12, s13, s23)
         assert abs(d / 2 * math.tan(math.radians(t1) / 2) - h1) < 0.06
         assert abs(d / 2 * math.tan(math.radians(t2) / 2) - h2) < 0.06
+
+
+# ---------------------------------------------------------------------------
+# Tensions of the model's own relaxed pair interfaces (oracle, FP64).
+# ---------------------------------------------------------------------------
+
+def _relaxed_band(sig, k, l, rho, steps=30000, ny=64):
+    import oracle
+    from paper_1904_12553_gb300 import workloads as W
+    w = W.pair_band(sig, k, l, rho=rho, ny=ny, beta=math.sqrt(0.06),
+                    steps=steps)
+    s = oracle.OracleSim(w.params)
+    s.init(w.c0)
+    s.step(steps)
+    m = s.moments()
+    s.close()
+    lam = oracle.lam(w.params)
+    T = LM.band_tension(m["phi"][:, :, 0], m["c"][:, :, 0], lam,
+                        math.sqrt(0.06), w.params["eta"])
+    third = [j for j in range(sig.shape[0]) if j not in (k, l)]
+    return T, float(np.abs(m["c"][third][:, :, 0]).max())
+
+
+def _sig3(s12, s13, s23):
+    return np.array([[0, s12, s13], [s12, 0, s23], [s13, s23, 0]], float)
+
+
+def test_pair_tension_of_equal_sigma_is_sigma():
+    """Equal tensions: every relaxed pair interface stays two-phase and its
+    discrete free-energy excess is sigma (to the 1% of W = 4 on the
+    lattice), the same for all pairs."""
+    sig = _sig3(0.01, 0.01, 0.01)
+    T = []
+    for k, l in ((0, 1), (0, 2), (1, 2)):
+        t, third = _relaxed_band(sig, k, l, [10.0, 1.0, 5.0])
+        assert third < 1e-3
+        T.append(t)
+    assert max(T) - min(T) < 1e-4 * 0.01
+    assert abs(T[0] / 0.01 - 1) < 0.01
+
+
+def test_unequal_sigma_pairs_adsorb_the_third_phase():
+    """With unequal tensions the model's pair interfaces are not two-phase:
+    in the paper's 0.6:0.6:1 ratio (sigma_min = 0.01, densities 10:1:5) the
+    third phase reaches several percent inside the drop's interfaces and
+    their tension falls by ~8% (recorded after 3e4 steps: 0.922 and 0.920
+    sigma, third phase 6.5% and 6.8%; the flat 2|3 interface 1.000 sigma).
+    Eq. N32 with these tensions gives 25.1 degrees where the nominal ones
+    give 33.6; the lens of the GPU tests settles at that angle. The 1:4/3:1
+    ratio: 85.6 and 47.2 degrees against the nominal 83.6 and 48.2."""
+    rho = [10.0, 1.0, 5.0]
+    for (s12, s13, s23), want, (lo, hi) in (
+            ((0.01, 0.01, 0.01 / 0.6), (25.15, 25.15), (0.90, 0.94)),
+            ((0.01, 0.04 / 3, 0.01), (85.6, 47.2), (0.96, 0.99))):
+        sig = _sig3(s12, s13, s23)
+        eff = {}
+        for k, l in ((0, 2), (1, 2), (0, 1)):
+            eff[(k, l)], third = _relaxed_band(sig, k, l, rho)
+            if (k, l) == (0, 2):
+                third13 = third
+        third = third13
+        r12 = eff[(0, 1)] / s12
+        assert lo < r12 < hi, r12
+        t1, t2 = LM.neumann(eff[(0, 1)], eff[(0, 2)], eff[(1, 2)])
+        assert abs(t1 - want[0]) < 0.4 and abs(t2 - want[1]) < 0.4, (t1, t2)
+        if s23 > s12:   # 0.6:0.6:1: phase 2 inside the 1|3 interface
+            assert third > 0.03

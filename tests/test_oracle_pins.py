@@ -557,3 +557,34 @@ def test_laplace_law():
     dp = m["p"][r < R / 2].mean() - m["p"][(m["c"][0] > 0.999) & (r > R + 12)].mean()
     assert abs(dp / (sig / R) - 1) < 0.05, dp / (sig / R)
     s.close()
+
+
+def test_absent_phase_chemical_potential_not_uniform():
+    """Reduction consistency (Section 4.1) holds only approximately in this
+    model: with the third of four phases absent (c_3 = 0 everywhere), c_3
+    evolves as m lap(mu_3) with mu_3 = sum_j Q_3j (rho_j + rho_N)/2 C_j
+    (Eqs. N12, N18, N24, equal mobilities), and mu_3 is not uniform across
+    the other phases' interfaces. Recorded: its range is of the order of
+    the chemical potentials themselves; the oracle generates c_3 > 1e-4
+    within 200 steps."""
+    w4 = W.paper_static_drops(4, absent=2, nx=120, ny=60, R=12.0)
+    w4.c0[0] = W.drop(120, 60, 30.0, 30.0, 12.0)
+    w4.c0[1] = W.drop(120, 60, 90.0, 30.0, 12.0)
+    w4.c0[3] = 1.0 - w4.c0[0] - w4.c0[1]
+    p = w4.params
+    s = oracle.OracleSim(p)
+    s.init(w4.c0)
+    C = s.chemical_potential()
+    rho = np.array(p["rho"])
+    g = 1.0 / rho
+    G = g.sum()
+    mu3 = sum((-g[2] * g[j] / G) * (rho[j] + rho[3]) / 2 * C[j]
+              for j in range(3) if j != 2)
+    mu3 = mu3 + (g[2] - g[2] * g[2] / G) * (rho[2] + rho[3]) / 2 * C[2]
+    spread = float(mu3.max() - mu3.min())
+    scale = float(np.abs(C).max())
+    assert spread > 0.1 * scale, (spread, scale)
+    s.step(200)
+    c3 = float(np.abs(s.moments()["c"][2]).max())
+    s.close()
+    assert c3 > 1e-4, c3

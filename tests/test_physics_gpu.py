@@ -3,7 +3,10 @@
 - Static drop (Section 4.1): the pressure jump of the FP32 and 16-bit storage
   forms agrees with the FP64 oracle's within 1%, and with sigma / R within 5%.
 - Liquid lens (Section 4.2): contact angles theta = 2 arctan(2 h / d) of the
-  equilibrated lens against the Neumann triangle, Eq. N32.
+  equilibrated lens against the Neumann triangle (Eq. N32), length and cap
+  heights against Eqs. N33/N34, for the paper's own case and the 256 x 256
+  set; with unequal tensions against the model's own pair tensions.
+- Reduction consistency (Section 4.1).
 """
 import math
 import os
@@ -97,56 +100,135 @@ def test_lens_precision_forms_2e4_steps(prec):
     assert max(abs(ang[0][0] - ang[1][0]), abs(ang[0][1] - ang[1][1])) <= 0.05
 
 
-def _lens_angles(s13, beta=0.0):
-    """Equilibrated lens (N=3, 256x256, walls in y, FP32, sigma_12 = 1e-3,
-    sigma_13 = sigma_23 = s13): stepped in chunks of 2e4 until both angles
-    move less than 0.05 degree per chunk (at most 1e6 steps)."""
+def _equilibrate(w, below, drop, chunk, tol, max_steps, prec=None):
+    """Step a lens in chunks until both angles move less than `tol` degrees
+    per chunk; returns (theta_1, theta_2, d, h_1, h_2, area, steps) from
+    circles fitted to the caps (lens_measure.measure_fit)."""
     from paper_1904_12553_gb300 import Solver
-    w = W.lens(nx=256, ny=256, R=40, s13=s13, precision="fp32", beta=beta)
-    s = Solver(w.params)
+    s = Solver({**w.params, **({"precision": prec} if prec else {})})
     s.init(w.c0)
-    prev, steps, drift = None, 0, None
-    while steps < 1_000_000:
-        s.step(20000)
-        steps += 20000
+    prev, steps = None, 0
+    while steps < max_steps:
+        s.step(chunk)
+        steps += chunk
         c = s.moments()["c"]
-        d, hu, hd, _ = LM.measure(c[0], c[2])
+        try:
+            d, hu, hd, _ = LM.measure_fit(c[below], c[drop])
+        except (ValueError, np.linalg.LinAlgError):  # no lens shape yet
+            prev = None
+            continue
         cur = LM.angles(d, hu, hd)
-        if prev is not None:
-            drift = max(abs(cur[0] - prev[0]), abs(cur[1] - prev[1]))
-            if drift < 0.05:
-                break
+        if prev is not None and max(abs(cur[0] - prev[0]),
+                                    abs(cur[1] - prev[1])) < tol:
+            break
         prev = cur
     s.close()
-    want = LM.neumann_symmetric(1e-3, s13)
-    print(f"\nlens s13={s13:g} beta={beta}: steps={steps} d={d:.1f} "
-          f"h=({hu:.1f}, {hd:.1f}) theta=({cur[0]:.2f}, {cur[1]:.2f}) "
-          f"neumann={want:.2f} rel=({cur[0] / want - 1:+.3f}, "
-          f"{cur[1] / want - 1:+.3f}) drift per 2e4 steps={drift:.3f} deg")
-    return cur, want
+    return cur[0], cur[1], d, hu, hd, LM.contour_area(c[drop]), steps
+
+
+def _effective_neumann(params, drop, up, low, ny=64, steps=30000):
+    """Eq. N32 with the model's own pair tensions: each pair's flat
+    interfaces relaxed on the GPU (FP64, a band of one phase in the other,
+    the third phase free to enter), tension = excess of the discrete free
+    energy (lens_measure.band_tension). Returns the (upper, lower) angles."""
+    import paper_1904_12553_gb300 as P
+    from paper_1904_12553_gb300 import Solver
+    sig = np.array(params["sigma"])
+    d = P.lbm_nphase_derive(params)
+    T = {}
+    for k, l in ((drop, up), (drop, low), (up, low)):
+        w = W.pair_band(sig, k, l, rho=params["rho"], ny=ny,
+                        beta=params["beta"], eta=params["eta"])
+        s = Solver(w.params)
+        s.init(w.c0)
+        s.step(steps)
+        m = s.moments()
+        s.close()
+        T[(k, l)] = LM.band_tension(m["phi"][:, :, 0], m["c"][:, :, 0],
+                                    d["lambda"], d["beta"], params["eta"])
+    return LM.neumann(T[(drop, up)], T[(drop, low)], T[(up, low)])
+
+
+@pytest.fixture(scope="module")
+def paper_lens_results():
+    """The paper's lens (Section 4.2: 150 x 150, R = 30, densities 10:1:5,
+    tau = 0.8, m = 0.1, eta = sqrt(2), beta = sqrt(0.06), walls in y,
+    sigma_min = 0.01), FP64, run to equilibrium (chunks of 2e4 steps, less
+    than 0.01 degree per chunk, at most 1.6e6 steps)."""
+    out = {}
+    for ratio in ("1:1:1", "1:4/3:1", "0.6:0.6:1"):
+        w = W.paper_lens(ratio)
+        sig = np.array(w.params["sigma"])
+        res = _equilibrate(w, 2, 0, 20000, 0.01, 1_600_000)
+        nom = LM.neumann(sig[0, 1], sig[0, 2], sig[1, 2])
+        eff = _effective_neumann(w.params, 0, 1, 2)
+        print(f"\npaper lens {ratio}: steps={res[6]} theta=({res[0]:.2f}, "
+              f"{res[1]:.2f}) d={res[2]:.2f} h=({res[3]:.2f}, {res[4]:.2f}) "
+              f"A={res[5]:.1f}; Eq. N32 nominal ({nom[0]:.2f}, {nom[1]:.2f}),"
+              f" with the model's pair tensions ({eff[0]:.2f}, {eff[1]:.2f})")
+        out[ratio] = (res, nom, eff)
+    return out
+
+
+def test_paper_lens_equal_tensions_matches_eqs_n32_n34(paper_lens_results):
+    """1:1:1: angles within 1% of Eq. N32 (60 degrees; 0.2% measured), and
+    d, h_1, h_2 within 2% of Eqs. N33/N34 at the drop's area (0.2%)."""
+    (t1, t2, d, h1, h2, A, _), nom, _ = paper_lens_results["1:1:1"]
+    assert abs(t1 / nom[0] - 1) <= 0.01 and abs(t2 / nom[1] - 1) <= 0.01
+    dd, g1, g2 = LM.lens_from_area(A, *nom)
+    assert abs(d / dd - 1) <= 0.02
+    assert abs(h1 / g1 - 1) <= 0.02 and abs(h2 / g2 - 1) <= 0.02
+
+
+@pytest.mark.parametrize("ratio", ["1:4/3:1", "0.6:0.6:1"])
+def test_paper_lens_unequal_tensions(paper_lens_results, ratio):
+    """Unequal tensions: the model's pair interfaces adsorb the third phase
+    and their tensions differ from the nominal sigma (see
+    test_lens_measure.py). The lens follows Eq. N32 with those tensions
+    within 1 degree (measured 0.2-0.3) and Eqs. N33/N34 at those angles
+    within 2% in d, h_1, h_2 (measured <= 1%). Against the nominal
+    tensions: 1:4/3:1 lands within 3% (85.8 and 47.0 against 83.6 and
+    48.2 degrees), the thin 0.6:0.6:1 lens at 25 degrees against 33.6 (its
+    angle passes 34 degrees about 3e4 steps in and keeps falling)."""
+    (t1, t2, d, h1, h2, A, _), nom, eff = paper_lens_results[ratio]
+    assert abs(t1 - eff[0]) <= 1.0 and abs(t2 - eff[1]) <= 1.0
+    dd, g1, g2 = LM.lens_from_area(A, *eff)
+    assert abs(d / dd - 1) <= 0.02
+    assert abs(h1 / g1 - 1) <= 0.02 and abs(h2 / g2 - 1) <= 0.02
+    if ratio == "1:4/3:1":
+        assert abs(t1 / nom[0] - 1) <= 0.03 and abs(t2 / nom[1] - 1) <= 0.03
 
 
 @pytest.fixture(scope="module")
 def lens_results():
-    return {s13: _lens_angles(s13) for s13 in (0.6e-3, 0.8e-3, 1.0e-3)}
+    """The 256 x 256 lens of the benchmark set (unit densities, sigma_12 =
+    1e-3, sigma_13 = sigma_23 = s13, beta from Eq. N36), FP32, run to
+    equilibrium (chunks of 4e4 steps, less than 0.01 degree per chunk, at
+    most 4e6 steps)."""
+    out = {}
+    for s13 in (0.6e-3, 0.8e-3, 1.0e-3):
+        w = W.lens(nx=256, ny=256, R=40, s13=s13, precision="fp32")
+        res = _equilibrate(w, 0, 2, 40000, 0.01, 4_000_000)
+        eff = _effective_neumann({**w.params, "precision": "fp64"}, 2, 1, 0)
+        nom = LM.neumann_symmetric(1e-3, s13)
+        print(f"\nlens s13={s13:g}: steps={res[6]} theta=({res[0]:.2f}, "
+              f"{res[1]:.2f}) d={res[2]:.1f} h=({res[3]:.1f}, {res[4]:.1f}); "
+              f"Eq. N32 nominal {nom:.2f}, with the model's pair tensions "
+              f"({eff[0]:.2f}, {eff[1]:.2f})")
+        out[s13] = (res, nom, eff)
+    return out
 
 
-@pytest.mark.parametrize("s13", [0.8e-3, 1.0e-3])
+@pytest.mark.parametrize("s13", [0.6e-3, 0.8e-3, 1.0e-3])
 def test_lens_neumann_angles(lens_results, s13):
-    """Resolved lenses (theta = 51.3 and 60 degrees): within 3% of Eq. N32
-    (1.0-2.0% measured when this test was written)."""
-    (t1, t2), want = lens_results[s13]
-    assert abs(t1 / want - 1) <= 0.03 and abs(t2 / want - 1) <= 0.03
-
-
-def test_thin_lens_and_ordering(lens_results):
-    """The thin lens (sigma_13 = 0.6e-3, theta = 33.6 degrees, ~22 nodes
-    high) carries the finite-interface error of W = 4: -13% measured when
-    this test was written. Angles must still rise with sigma_13 as Eq. N32
-    says."""
-    (t1, t2), want = lens_results[0.6e-3]
-    assert abs(t1 / want - 1) <= 0.15 and abs(t2 / want - 1) <= 0.15
-    th = [sum(lens_results[s][0]) / 2 for s in (0.6e-3, 0.8e-3, 1.0e-3)]
+    """Both caps within 1 degree of Eq. N32 with the model's own pair
+    tensions; the resolved lenses (51.3 and 60 degrees nominal) also within
+    3% of the nominal angle."""
+    (t1, t2, *_), nom, eff = lens_results[s13]
+    assert abs(t1 - eff[0]) <= 1.0 and abs(t2 - eff[1]) <= 1.0
+    if s13 > 0.7e-3:
+        assert abs(t1 / nom - 1) <= 0.03 and abs(t2 / nom - 1) <= 0.03
+    th = [sum(lens_results[s][0][:2]) / 2 for s in (0.6e-3, 0.8e-3, 1.0e-3)]
     assert th[0] < th[1] < th[2]
 
 
@@ -290,3 +372,45 @@ def test_paper_five_phase_motion():
     assert np.abs(m1 / m0 - 1).max() <= 1e-10
     assert y1 < y2 < 280 and y3 > 40
     assert math.isfinite(ke)
+
+
+def test_reduction_consistency_four_phases_one_absent():
+    """Section 4.1's reduction test: the paper's four-phase static drops
+    (300 x 100, densities 20:1:10:5, sigma = 0.01, m = 0.001) with the third
+    phase absent against the three-phase run (20:1:5), FP64, 2e4 steps.
+
+    The model does not keep the absent phase at exactly zero (its chemical
+    potential combination is not uniform at the other interfaces; see the
+    oracle test of the start state), so the runs are "almost identical":
+    measured after 2e4 steps max c_3 = 1.6e-3, the other fractions within
+    1.2e-3 of the three-phase run, velocities within 1.3e-6 (max |u| 6.5e-6).
+    Asserted at those levels with a margin of about 1.5; the FP64 path is
+    first checked against the oracle on this geometry."""
+    from paper_1904_12553_gb300 import Solver
+    w4 = W.paper_static_drops(4, absent=2)
+    w3 = W.paper_static_drops(3)
+    s = Solver(w4.params)
+    s.init(w4.c0)
+    s.step(200)
+    g = s.moments()
+    o = oracle.run(w4.params, w4.c0, steps=200)
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-12
+    assert np.abs(g["u"] - o["u"]).max() <= 1e-14
+    s.step(20000 - 200)
+    m4 = s.moments()
+    s.close()
+    s = Solver(w3.params)
+    s.init(w3.c0)
+    s.step(20000)
+    m3 = s.moments()
+    s.close()
+    dc = [float(np.abs(m4["c"][a] - m3["c"][b]).max())
+          for a, b in ((0, 0), (1, 1), (3, 2))]
+    c3 = float(np.abs(m4["c"][2]).max())
+    du = float(np.abs(m4["u"] - m3["u"]).max())
+    print(f"\nreduction: max|dc| (1, 2, background) = {dc[0]:.2e}, "
+          f"{dc[1]:.2e}, {dc[2]:.2e}; max c_3 = {c3:.2e}; max|du| = {du:.2e}"
+          f" (max|u| {np.abs(m3['u']).max():.2e})")
+    assert max(dc) <= 2e-3
+    assert c3 <= 2.5e-3
+    assert du <= 2e-6
