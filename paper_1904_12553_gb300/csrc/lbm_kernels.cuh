@@ -104,6 +104,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_S(float v) {
   return __ushort_as_bfloat16((unsigned short)(u >> 16));
 }
 template <> __device__ __forceinline__ __half to_S(float v) { return __float2half_rn(v); }
+// Two values at once with the packed conversion (round to nearest even, the
+// same bits as to_S): one instruction for two stores of the 16-bit forms.
+__device__ __forceinline__ void to_S2(float a, float b, __nv_bfloat16 &ra, __nv_bfloat16 &rb) {
+  const __nv_bfloat162 r = __floats2bfloat162_rn(a, b); ra = r.x; rb = r.y; }
+__device__ __forceinline__ void to_S2(float a, float b, __half &ra, __half &rb) {
+  const __half2 r = __floats2half2_rn(a, b); ra = r.x; rb = r.y; }
+__device__ __forceinline__ void to_S2(float a, float b, float &ra, float &rb) { ra = a; rb = b; }
+__device__ __forceinline__ void to_S2(double a, double b, double &ra, double &rb) { ra = a; rb = b; }
 template <> __device__ __forceinline__ float to_S(float v) { return v; }
 template <typename S> __device__ __forceinline__ S to_S(double v) { return v; }
 
@@ -602,6 +610,7 @@ __device__ __forceinline__ void collide_stream(
   const T C1 = T(3) * ff, D1 = T(9) * ff;
   const T E1 = T(3) * ff, E2 = T(4.5) * ff * a.jfac;
   const T keep_g = T(1) - tg;
+  T gv[9];
 #pragma unroll
   for (int k = 1; k < 9; ++k) {
     const T cxk = T(cx_of(k)), cyk = T(cy_of(k));
@@ -612,15 +621,20 @@ __device__ __forceinline__ void collide_stream(
       inner += E1 * (cxk * m.grx + cyk * m.gry) + E2 * (cxk * m.Jx + cyk * m.Jy);
     const T t = A0 + C1 * cF + cu * inner;
     const int kk = dk[k];
-    if constexpr (Prec<P>::REF)
-      a.gm_out[(size_t)(kk - 1) * V + dst[k]] = to_S<typename Prec<P>::Sm>(
-          keep_g * g[k] + a.sg_st * t -
-          g_refp(cdotu(kk, ux, uy), ux, uy, pr, a.rho_base * a.sg_st, T(3) * a.sg_st));
-    else if constexpr (MIX)
-      a.gm_out[(size_t)(kk - 1) * V + dst[k]] =
-          to_S<typename Prec<P>::Sm>(keep_g * g[k] + a.sg_st * t);
+    if constexpr (MIX)  // relative to the equilibrium's parts at this node
+      gv[k] = keep_g * g[k] + a.sg_st * t -
+          g_refp(cdotu(kk, ux, uy), ux, uy, pr, a.rho_base * a.sg_st, T(3) * a.sg_st);
     else
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] = keep_g * g[k] + w_of<T>(k) * t;
+  }
+  if constexpr (MIX) {  // converted two at a time
+#pragma unroll
+    for (int k = 1; k < 9; k += 2) {
+      typename Prec<P>::Sm s0, s1;
+      to_S2(gv[k], gv[k + 1], s0, s1);
+      a.gm_out[(size_t)(dk[k] - 1) * V + dst[k]] = s0;
+      a.gm_out[(size_t)(dk[k + 1] - 1) * V + dst[k + 1]] = s1;
+    }
   }
 
   // CH collisions (Eq. N24) with h^eq (Eq. N25) and R_k (Eqs. N26, N27),
@@ -642,23 +656,32 @@ __device__ __forceinline__ void collide_stream(
     }
     const T keep = T(1) - ti;
     T moving_sum = T(0);
+    if constexpr (MIX) {
+      // relative to the advective part at this node (the slots' source),
+      // converted two at a time; the mass balance uses each value as the
+      // reader will decode it
+      T hv[9], rf[9];
 #pragma unroll
-    for (int k = 1; k < 9; ++k) {
-      const T t = al + T(cx_of(k)) * bx + T(cy_of(k)) * by;
-      const int kk = dk[k];
-      if constexpr (MIX) {
-        // REF: relative to the advective part at this node, the slot's source
-        const T ref = Prec<P>::REF ? adv_units(cdotu(kk, ux, uy), ph, T(3) * a.sh_st)
-                                   : T(0);
-        const auto sv = to_S<typename Prec<P>::Sm>(keep * hreg[i][k] + t - ref);
-        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = sv;
-        // the mass balance uses the value as the reader will decode it
-        moving_sum = __fmaf_rn(w_of<T>(kk) * a.sh_ld,
-                               Prec<P>::REF ? __fadd_rn(to_T(sv), ref) : to_T(sv),
+      for (int k = 1; k < 9; ++k) {
+        const T t = al + T(cx_of(k)) * bx + T(cy_of(k)) * by;
+        rf[k] = adv_units(cdotu(dk[k], ux, uy), ph, T(3) * a.sh_st);
+        hv[k] = keep * hreg[i][k] + t - rf[k];
+      }
+      typename Prec<P>::Sm sv[9];
+#pragma unroll
+      for (int k = 1; k < 9; k += 2) to_S2(hv[k], hv[k + 1], sv[k], sv[k + 1]);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) {
+        a.hm_out[((size_t)(i * 8 + dk[k] - 1)) * V + dst[k]] = sv[k];
+        moving_sum = __fmaf_rn(w_of<T>(dk[k]) * a.sh_ld, __fadd_rn(to_T(sv[k]), rf[k]),
                                moving_sum);
-      } else {
+      }
+    } else {
+#pragma unroll
+      for (int k = 1; k < 9; ++k) {
+        const T t = al + T(cx_of(k)) * bx + T(cy_of(k)) * by;
         const T hs = keep * hreg[i][k] + w_of<T>(k) * t;
-        a.hm_out[((size_t)(i * 8 + kk - 1)) * V + dst[k]] = hs;
+        a.hm_out[((size_t)(i * 8 + dk[k] - 1)) * V + dst[k]] = hs;
         moving_sum = __fadd_rn_T(moving_sum, hs);
       }
     }
