@@ -496,6 +496,7 @@ lbm_status lbm_nphase_create(const lbm_nphase_params *p, void *ws,
   g.u_prev[0] = base + L.u_prev;
   g.u_prev[1] = base + L.u_prev + upb;
   h->stage = (double *)(base + L.stage);
+  g.scratch = h->stage;
   g.red = (double *)(base + L.red);
   g.red_out = (double *)(base + L.red_out);
   g.err = (int *)(base + L.err);

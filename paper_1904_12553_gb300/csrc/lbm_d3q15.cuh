@@ -934,20 +934,26 @@ __global__ void __launch_bounds__(MT3, 1)
   }
 }
 
+// As init_phi_kernel: phi_i also to phid[i][V] in FP64 (phid may be c).
 template <int P, int NP>
-__global__ void init3_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
-                                 const double *__restrict__ u, double r0,
-                                 double r1, double r2, double r3, double r4) {
+__global__ void init3_phi_kernel(const KArgs<P> a, const double *c,
+                                 const double *__restrict__ u, double *phid,
+                                 double r0, double r1, double r2, double r3,
+                                 double r4) {
   typedef typename Prec<P>::T T;
   const double rt[5] = {r0, r1, r2, r3, r4};
   const double rN = rt[NP];
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < a.V;
        q += (size_t)gridDim.x * blockDim.x) {
     const double cN = c[(size_t)NP * a.V + q];
+    double ph[NP];
     for (int i = 0; i < NP; ++i) {
       const double ci = c[(size_t)i * a.V + q];
-      a.pp_out[(size_t)i * a.V + q] =
-          (T)((2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN));
+      ph[i] = (2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN);
+    }
+    for (int i = 0; i < NP; ++i) {
+      a.pp_out[(size_t)i * a.V + q] = (T)ph[i];
+      phid[(size_t)i * a.V + q] = ph[i];
     }
     for (int d = 0; d < 3; ++d) a.u_out[(size_t)d * a.V + q] = u ? (T)u[(size_t)d * a.V + q] : T(0);
   }
@@ -958,14 +964,11 @@ __global__ void init3_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
 // constants `d`, each stored value rounded once into its form.
 template <int P, int NP, bool WALL>
 __global__ void init3_pop_kernel(const KArgs3<P> A, const KArgs<LBM_FP64> d,
-                                 const double *__restrict__ cin,
-                                 const double *__restrict__ uin, double p0,
-                                 double r0, double r1, double r2, double r3,
-                                 double r4) {
+                                 const double *__restrict__ phid,
+                                 const double *__restrict__ uin, double p0) {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
   const KArgs<P> &a = A.a;
-  const double rt[5] = {r0, r1, r2, r3, r4};
   const int nx = a.nx, ny = a.ny, nz = A.nz;
   const size_t V = a.V;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < V;
@@ -978,7 +981,7 @@ __global__ void init3_pop_kernel(const KArgs3<P> A, const KArgs<LBM_FP64> d,
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx)
             s[((dz + 1) * 3 + dy + 1) * 3 + dx + 1] =
-                phi_of_c<NP>(cin, V, node3<WALL>(x + dx, y + dy, z + dz, nx, ny, nz), i, rt);
+                phid[(size_t)i * V + node3<WALL>(x + dx, y + dy, z + dz, nx, ny, nz)];
       double gtmp[3];
       ph[i] = s[13];
       stencil3<double, 3, 3>(s, 1, 1, 1, gtmp, lp[i]);
@@ -1172,16 +1175,14 @@ cudaError_t launch_init3_np(const Consts &c, const Grid &g, int cur,
   size_t blocks = (g.V + threads - 1) / threads;
   if (blocks > 65535u * 16u) blocks = 65535u * 16u;
   init3_phi_kernel<P, NP><<<(unsigned)blocks, threads, 0, s>>>(
-      A.a, cin, uin, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+      A.a, cin, uin, g.scratch, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const KArgs<LBM_FP64> d = make_args<LBM_FP64>(c, g, cur ^ 1, MODE_STEP, Outputs{});
   if (wall)
-    init3_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(
-        A, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+    init3_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(A, d, g.scratch, uin, p0);
   else
-    init3_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(
-        A, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+    init3_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(A, d, g.scratch, uin, p0);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,10 @@ struct Consts {
 // TMA descriptors of one state buffer for the pipelined step kernel.
 struct TmaMaps {
   CUtensorMap hm, h0, pp, gm, up;
+  // FP32 pipelined kernel: the halo column and row that wrap around a
+  // periodic grid (boxes of 16 bytes x the box height, and one row x the
+  // box width, of the h, d_0 and phi(t-1) arrays)
+  CUtensorMap hmx, h0x, ppx, hmy, h0y, ppy;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType,
@@ -66,6 +70,8 @@ struct Grid {
   double *red;      // per-block partial sums of the diagnostics
   double *red_out;  // N + 2 reduced diagnostics
   int *err;         // device error word (1: a bounded wait gave up)
+  double *scratch;  // FP64 staging of host inputs and outputs ([N + D][V]);
+                    // initialisation keeps phi_i there ([N-1][V])
   int grad_scheme;  // 0: central (Eq. N31a), 1: mixed (Eq. N40)
   bool use_tma;     // pipelined kernel usable for this grid
   bool march3;      // D3Q15 step by the z-marching kernel

@@ -908,8 +908,13 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 //    from global memory before the wait instead of staged -19% (a third
 //    stage on top, a further -6%); releasing the stage after the phi
 //    barrier (one barrier per tile) -9%; the ring's phi split over
-//    (position, phase) pairs on all warps -1.5%. Instrumented, the kernel
-//    spends 13-19% of its time in the stage wait.
+//    (position, phase) pairs on all warps -1.5%; the stage refilled right
+//    after the phi barrier (two barriers kept) -9%; 32 x 4 tiles with two
+//    CTAs per SM (four stages in flight per SM) -27%; an L2 prefetch of the
+//    tile one, two or four beyond the stages (cp.async.bulk.prefetch.tensor)
+//    -35%, -37%, -48%. Instrumented, the kernel spends 13-19% of its time in
+//    the stage wait; ncu counts it as long-scoreboard stalls (1.5 per
+//    issued instruction).
 //  - 16-bit with the source-relative encoding: one CTA per SM with one
 //    barrier and a double-buffered phi tile -20% (3 stages -22%); the ring's
 //    decode spread over all warps -6%. With plain scaled storage (an earlier
@@ -938,6 +943,10 @@ template <int P> struct TmaGeom {
   static constexpr int UH = REF ? HBP : TBY;
   static constexpr int UOX = REF ? HXR : 0, UOY = REF ? RY : 0;
   static constexpr int UPN = REF ? 3 : 2;           // u(t-1) planes (+ p(t-1))
+  // FP32: the ring column and row that wrap around a periodic grid are
+  // staged too (x: 16 bytes of columns at the far edge x box height; y: one
+  // row x box width at the far edge), for tiles on the grid's edge.
+  static constexpr bool WRAP = WIDE;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -992,7 +1001,16 @@ template <int P, int NP> struct TmaStage {
   static constexpr size_t PP = al((size_t)NP * G::HBP * G::WR * sizeof(T));
   static constexpr size_t GM = al((size_t)8 * G::TBY * BX * sizeof(Sm));
   static constexpr size_t UP = al((size_t)G::UPN * G::UH * G::UW * sizeof(T));
-  static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
+  // wrapped halo column (x) and row (y) of the h, d_0, phi(t-1) arrays
+  static constexpr size_t XHM = al((size_t)8 * NP * G::HB * G::HXM * sizeof(Sm));
+  static constexpr size_t XH0 = al((size_t)NP * G::HB * G::HXR * sizeof(T));
+  static constexpr size_t XPP = al((size_t)NP * G::HBP * G::HXR * sizeof(T));
+  static constexpr size_t YHM = al((size_t)8 * NP * G::WM * sizeof(Sm));
+  static constexpr size_t YH0 = al((size_t)NP * G::WR * sizeof(T));
+  static constexpr size_t YPP = YH0;
+  static constexpr size_t WRAPB = G::WRAP ? XHM + XH0 + XPP + YHM + YH0 + YPP : 0;
+  static constexpr size_t BASE = HM + H0 + PP + GM + UP;  // offset of the wrap boxes
+  static constexpr size_t BYTES = BASE + WRAPB;
   // bytes the TMA engine writes per stage (full boxes, including fill)
   static constexpr uint32_t TX =
       (uint32_t)((size_t)8 * NP * G::HB * G::WM * sizeof(Sm) +
@@ -1000,6 +1018,11 @@ template <int P, int NP> struct TmaStage {
                  (size_t)NP * G::HBP * G::WR * sizeof(T) +
                  (size_t)8 * G::TBY * BX * sizeof(Sm) +
                  (size_t)G::UPN * G::UH * G::UW * sizeof(T));
+  static constexpr uint32_t XTX =
+      (uint32_t)(((size_t)8 * NP * G::HB * G::HXM) * sizeof(Sm) +
+                 ((size_t)NP * G::HB * G::HXR + (size_t)NP * G::HBP * G::HXR) * sizeof(T));
+  static constexpr uint32_t YTX =
+      (uint32_t)((size_t)8 * NP * G::WM * sizeof(Sm) + (size_t)2 * NP * G::WR * sizeof(T));
   static constexpr size_t SPHI = al((size_t)NP * (G::TBY + 2) * (BX + 2) * sizeof(T));
   static constexpr int S = G::S;
   static constexpr size_t SMEM = S * BYTES + SPHI + 64;
@@ -1040,18 +1063,45 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
   const int nx = a.nx, ny = a.ny;
   const int nmine = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
+  // FP32 tiles on the edge of a periodic grid: which wrapped halo column
+  // (1: x = -1, staged from x = nx - 4 .. nx - 1; 2: x = nx, from 0 .. 3)
+  // and row (1: y = -1 from ny - 1; 2: y = ny from 0; none with walls,
+  // whose ghost rows repeat a row of the box) are staged with the tile.
+  auto halo_x = [&](int x0) {
+    return !G::WRAP ? 0 : (x0 == 0 ? 1 : (x0 + BX == nx ? 2 : 0));
+  };
+  auto halo_y = [&](int y0) {
+    return (!G::WRAP || WALL) ? 0 : (y0 == 0 ? 1 : (y0 + TBY == ny ? 2 : 0));
+  };
   auto issue = [&](int j) {  // thread 0: TMA loads of my j-th tile
     const int t = blockIdx.x + j * gridDim.x;
     const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
     unsigned char *st = smem + (j % S) * St::BYTES;
     uint64_t *b = bar + (j % S);
-    mbar_expect_tx(b, St::TX);
+    const int wx = halo_x(x0), wy = halo_y(y0);
+    mbar_expect_tx(b, St::TX + (wx ? St::XTX : 0u) + (wy ? St::YTX : 0u));
     tma_load_3d(st, &maps.hm, x0 - G::HXM, y0 - 1, 0, b);
     tma_load_3d(st + St::HM, &maps.h0, x0 - G::HXR, y0 - 1, 0, b);
     tma_load_3d(st + St::HM + St::H0, &maps.pp, x0 - G::HXR, y0 - G::RY, 0, b);
     tma_load_3d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, 0, b);
     tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0 - G::UOX,
                 y0 - G::UOY, 0, b);
+    if constexpr (G::WRAP) {
+      unsigned char *w = st + St::BASE;
+      if (wx) {
+        const int xs = wx == 1 ? nx - G::HXR : 0;
+        tma_load_3d(w, &maps.hmx, xs, y0 - 1, 0, b);
+        tma_load_3d(w + St::XHM, &maps.h0x, xs, y0 - 1, 0, b);
+        tma_load_3d(w + St::XHM + St::XH0, &maps.ppx, xs, y0 - 1, 0, b);
+      }
+      if (wy) {
+        const int ys = wy == 1 ? ny - 1 : 0;
+        w += St::XHM + St::XH0 + St::XPP;
+        tma_load_3d(w, &maps.hmy, x0 - G::HXM, ys, 0, b);
+        tma_load_3d(w + St::YHM, &maps.h0y, x0 - G::HXR, ys, 0, b);
+        tma_load_3d(w + St::YHM + St::YH0, &maps.ppy, x0 - G::HXR, ys, 0, b);
+      }
+    }
   };
 
   if (tid == 0) {
@@ -1122,7 +1172,20 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
 
     // phi on the tile and its ring. A position whose node lies inside the
     // array without wrapping reads the staged box; others read global memory.
-    auto box_phi = [&](int bxm, int bxr, int by, T *err) {
+    // phi at a position of a staged wrap box: planes `pm` / `pr` apart,
+    // the position at offsets om / orr in them, into sphi[.][o]
+    auto wrap_phi = [&](const Sm *hmb, const T *h0b, const T *ppb, int pm, int pr,
+                        int om, int orr, int o) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T mov[8], e;
+#pragma unroll
+        for (int k = 1; k < 9; ++k) mov[k - 1] = to_T(hmb[(i * 8 + k - 1) * pm + om]);
+        sphi[i * PL + o] = node_phi<P>(h0b[i * pr + orr], mov, ppb[i * pr + orr], e, a.sh_ld);
+      }
+    };
+    // (the result goes to sphi row `out_row`, by default the box row)
+    auto box_phi = [&](int bxm, int bxr, int by, T *err, int out_row = -1) {
       T mv[NP][8];
 #pragma unroll
       for (int i = 0; i < NP; ++i)
@@ -1147,7 +1210,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
         const T rest = sh0[(i * G::HB + by) * G::WR + bxr];
         const T pp = spp[(i * G::HBP + by - 1 + G::RY) * G::WR + bxr];
         T e;
-        sphi[i * PL + by * SW + (bxr - G::HXR + 1)] =
+        sphi[i * PL + (out_row < 0 ? by : out_row) * SW + (bxr - G::HXR + 1)] =
             node_phi<P>(rest, mov, pp, e, a.sh_ld);
         if (err) err[i] = e;
       }
@@ -1192,11 +1255,35 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
       int lx, ly;
       ring_pos_1<TBY>(tid, lx, ly);
       const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
-      if (rx >= 0 && rx < nx && ry >= 0 && ry < ny)
+      const bool inx = rx >= 0 && rx < nx, iny = ry >= 0 && ry < ny;
+      if (inx && iny) {
         box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, ly, nullptr);
-      else
+      } else if constexpr (G::WRAP) {
+        // staged wrapped column or row, a wall's ghost row from the box, or
+        // (corners, ragged tails) global memory
+        const int wx = halo_x(x0), wy = halo_y(y0);
+        const unsigned char *w = st + St::BASE;
+        if (iny && ((rx < 0 && wx == 1) || (rx >= nx && wx == 2))) {
+          const int c = rx < 0 ? G::HXR - 1 : 0;
+          wrap_phi((const Sm *)w, (const T *)(w + St::XHM),
+                   (const T *)(w + St::XHM + St::XH0), G::HB * G::HXM,
+                   G::HB * G::HXR, ly * G::HXM + c, ly * G::HXR + c, ly * SW + lx);
+        } else if (inx && WALL) {
+          box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, wrap_y<WALL>(ry, ny) - y0 + 1,
+                  nullptr, ly);
+        } else if (inx && ((ry < 0 && wy == 1) || (ry >= ny && wy == 2))) {
+          w += St::XHM + St::XH0 + St::XPP;
+          wrap_phi((const Sm *)w, (const T *)(w + St::YHM),
+                   (const T *)(w + St::YHM + St::YH0), G::WM, G::WR,
+                   lx - 1 + G::HXM, lx - 1 + G::HXR, ly * SW + lx);
+        } else {
+          phi_global<P, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
+                                  ly * SW + lx);
+        }
+      } else {
         phi_global<P, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
-                          ly * SW + lx);
+                                ly * SW + lx);
+      }
     }
     // phi of the tile and its ring complete (and the decision to stop
     // CTA-wide).
@@ -1240,21 +1327,29 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
 // Initialisation: phi from c (inverse of Eqs. N2, N12), then h = h^eq and
 // g = g^eq at the stencil C_i.
 // ---------------------------------------------------------------------------
+// phi_i (FP64) goes to phid[i][V] as well, for the stencils of the start;
+// phid may be the array c came in (each node reads its own c first).
 template <int P, int NP>
-__global__ void init_phi_kernel(const KArgs<P> a, const double *__restrict__ c,
-                                const double *__restrict__ u, double r0,
-                                double r1, double r2, double r3, double r4) {
+__global__ void init_phi_kernel(const KArgs<P> a, const double *c,
+                                const double *__restrict__ u, double *phid,
+                                double r0, double r1, double r2, double r3,
+                                double r4) {
   typedef typename Prec<P>::T T;
   const double rt[5] = {r0, r1, r2, r3, r4};
   const double rN = rt[NP];
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < a.V;
        q += (size_t)gridDim.x * blockDim.x) {
     const double cN = c[(size_t)NP * a.V + q];
+    double ph[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       const double ci = c[(size_t)i * a.V + q];
-      const double ph = (2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN);
-      a.pp_out[(size_t)i * a.V + q] = (T)ph;
+      ph[i] = (2.0 * (rt[i] * ci - rN * cN) - (rt[i] - rN)) / (rt[i] + rN);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      a.pp_out[(size_t)i * a.V + q] = (T)ph[i];
+      phid[(size_t)i * a.V + q] = ph[i];
     }
     a.u_out[q] = u ? (T)u[q] : T(0);
     a.u_out[a.V + q] = u ? (T)u[a.V + q] : T(0);
@@ -1283,32 +1378,17 @@ template <> __device__ __forceinline__ __half store_once(double v) {
   return to_S<__half>(float_round_odd(v));
 }
 
-// Order parameter phi_i of node q from the volume fractions (inverse of
-// Eqs. N2 and N12), in FP64.
-template <int NP>
-__device__ __forceinline__ double phi_of_c(const double *__restrict__ c,
-                                           size_t V, size_t q, int i,
-                                           const double *rt) {
-  const double rN = rt[NP];
-  return (2.0 * (rt[i] * c[(size_t)i * V + q] - rN * c[(size_t)NP * V + q]) -
-          (rt[i] - rN)) /
-         (rt[i] + rN);
-}
-
-// Equilibrium start in FP64 for every storage form: phi and its Laplacian
-// from the volume fractions, C_i (Eqs. N17, N18), h^eq (Eq. N25) and g^eq
+// Equilibrium start in FP64 for every storage form: phi (FP64, from
+// init_phi_kernel) and its Laplacian, C_i (Eqs. N17, N18), h^eq (Eq. N25) and g^eq
 // (Eq. 25) are computed in double with the constants `d`, and each stored
 // value is rounded once into its form. The 16-bit references (and the FP32
 // phi(t-1), u(t-1) they use) are those the step kernel decodes with.
 template <int P, int NP, bool WALL>
 __global__ void init_pop_kernel(const KArgs<P> a, const KArgs<LBM_FP64> d,
-                                const double *__restrict__ cin,
-                                const double *__restrict__ uin, double p0,
-                                double r0, double r1, double r2, double r3,
-                                double r4) {
+                                const double *__restrict__ phid,
+                                const double *__restrict__ uin, double p0) {
   typedef typename Prec<P>::T T;
   typedef typename Prec<P>::Sm Sm;
-  const double rt[5] = {r0, r1, r2, r3, r4};
   const int nx = a.nx, ny = a.ny;
   const size_t V = a.V;
   T *h0 = a.h0_out;
@@ -1325,8 +1405,8 @@ __global__ void init_pop_kernel(const KArgs<P> a, const KArgs<LBM_FP64> d,
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx)
-          s[(dy + 1) * 3 + dx + 1] = phi_of_c<NP>(
-              cin, V, (size_t)wrap_y<WALL>(y + dy, ny) * nx + wrap(x + dx, nx), i, rt);
+          s[(dy + 1) * 3 + dx + 1] =
+              phid[(size_t)i * V + (size_t)wrap_y<WALL>(y + dy, ny) * nx + wrap(x + dx, nx)];
       ph[i] = s[4];
       lp[i] = laplacian<double, 3>(s, 1, 1);
     }
@@ -1488,6 +1568,13 @@ bool encode_tma_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
                 enc3(&m.pp, g.phi_prev[b], sizeof(T), NP, G::WR, G::HBP, NP) &&
                 enc3(&m.gm, g.gm[b], sizeof(Sm), 8, BX, G::TBY, 8) &&
                 enc3(&m.up, g.u_prev[b], sizeof(T), G::UPN, G::UW, G::UH, G::UPN);
+      if (G::WRAP)
+        ok = ok && enc3(&m.hmx, g.hm[b], sizeof(Sm), 8 * NP, G::HXM, G::HB, 8 * NP) &&
+             enc3(&m.h0x, g.h0[b], sizeof(T), NP, G::HXR, G::HB, NP) &&
+             enc3(&m.ppx, g.phi_prev[b], sizeof(T), NP, G::HXR, G::HBP, NP) &&
+             enc3(&m.hmy, g.hm[b], sizeof(Sm), 8 * NP, G::WM, 1, 8 * NP) &&
+             enc3(&m.h0y, g.h0[b], sizeof(T), NP, G::WR, 1, NP) &&
+             enc3(&m.ppy, g.phi_prev[b], sizeof(T), NP, G::WR, 1, NP);
       if (!ok) return false;
     }
     return true;
@@ -1505,16 +1592,14 @@ cudaError_t launch_init_np(const Consts &c, const Grid &g, int cur,
   size_t blocks = (g.V + threads - 1) / threads;
   if (blocks > 65535u * 16u) blocks = 65535u * 16u;
   init_phi_kernel<P, NP><<<(unsigned)blocks, threads, 0, s>>>(
-      a, cin, uin, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+      a, cin, uin, g.scratch, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const KArgs<LBM_FP64> d = make_args<LBM_FP64>(c, g, cur ^ 1, MODE_STEP, Outputs{});
   if (wall)
-    init_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(
-        a, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+    init_pop_kernel<P, NP, true><<<(unsigned)blocks, threads, 0, s>>>(a, d, g.scratch, uin, p0);
   else
-    init_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(
-        a, d, cin, uin, p0, c.rho_t[0], c.rho_t[1], c.rho_t[2], c.rho_t[3], c.rho_t[4]);
+    init_pop_kernel<P, NP, false><<<(unsigned)blocks, threads, 0, s>>>(a, d, g.scratch, uin, p0);
   return cudaGetLastError();
 }
 
