@@ -1045,7 +1045,16 @@ __device__ __forceinline__ void ring_pos_1(int r, int &lx, int &ly) {
   }
 }
 
-template <int P, int NP, bool WALL>
+// WHOLE: the grid is whole tiles, more than one in each direction. Its
+// edge tiles' boxes are then made periodic before use: the box column (x)
+// and row (y, periodic grids) beyond the grid that the ring reads (and, in
+// the 16-bit forms, the two that the sources read) are overwritten with the
+// wrapped values from global memory, loaded before the stage's wait. Every
+// tile then reads every position from its boxes at fixed offsets (a wall's
+// ghost row is the adjacent row; a source behind a wall is the node
+// itself): one branch-free path for all tiles. Other grids take a general
+// path that reads wrapped positions from global memory.
+template <int P, int NP, bool WALL, bool WHOLE>
 __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
     tile_kernel_tma(const KArgs<P> a, const __grid_constant__ TmaMaps maps,
                     int ntx, int ntiles) {
@@ -1117,39 +1126,144 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
     const int t = blockIdx.x + j * gridDim.x;
     const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
     T *sphi = (T *)(smem + S * St::BYTES);
-    const unsigned char *st = smem + (j % S) * St::BYTES;
+    unsigned char *stw = smem + (j % S) * St::BYTES;
+    const unsigned char *st = stw;
     const Sm *shm = (const Sm *)st;
     const T *sh0 = (const T *)(st + St::HM);
     const T *spp = (const T *)(st + St::HM + St::H0);
     const Sm *sgm = (const Sm *)(st + St::HM + St::H0 + St::PP);
     const int gx = x0 + tx, gy = y0 + ty;
-    const bool active = gx < nx && gy < ny;
+    const bool active = WHOLE || (gx < nx && gy < ny);
     const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
+
+    // ---- the periodic patch of an edge tile (16-bit forms, WHOLE grids;
+    // FP32 stages its wrapped halo by TMA instead, above) ----
+    // Entries: x: hm and h0 one column, phi(t-1) and u(t-1) NC columns on
+    // the wrapped side; y: hm, h0 one row, phi(t-1) and u(t-1) NC rows.
+    // Entry e -> array (0 hm, 1 h0, 2 phi(t-1), 3 u(t-1)), plane and box
+    // position.
+    constexpr bool PATCH = G::REF && WHOLE;
+    constexpr int NC = 2;                        // columns / rows of the sources
+    constexpr int UPP = G::UPN;                  // u(t-1) planes patched
+    constexpr int NXS = (9 * NP) * G::HB + NC * (NP * G::HBP + UPP * G::UH);
+    constexpr int NYS = (9 * NP) * (BX + 2) + NC * (NP + UPP) * (BX + 2 * NC);
+    constexpr int PM = PATCH ? (NXS + NYS + G::NTH - 1) / G::NTH : 1;
+    const bool patch_x = PATCH && (x0 == 0 || x0 + BX == nx);
+    const bool patch_y = PATCH && !WALL && (y0 == 0 || y0 + TBY == ny);
+    const int nxs = patch_x ? NXS : 0, nys = patch_y ? NYS : 0;
+    auto entry = [&](int e, int &arr, int &pl, int &bx, int &by) {
+      const bool left = x0 == 0, bottom = y0 == 0;
+      if (e < nxs) {
+        int f = e;
+        if (f < 8 * NP * G::HB) {
+          arr = 0; pl = f / G::HB; by = f % G::HB; bx = left ? G::HXM - 1 : G::HXM + BX;
+        } else if ((f -= 8 * NP * G::HB) < NP * G::HB) {
+          arr = 1; pl = f / G::HB; by = f % G::HB; bx = left ? G::HXR - 1 : G::HXR + BX;
+        } else {
+          f -= NP * G::HB;
+          const int two = f % NC;
+          f /= NC;
+          if (f < NP * G::HBP) {
+            arr = 2; pl = f / G::HBP; by = f % G::HBP;
+          } else {
+            f -= NP * G::HBP;
+            arr = 3; pl = f / G::UH; by = f % G::UH;
+          }
+          bx = left ? G::HXR - NC + two : G::HXR + BX + two;
+        }
+      } else {
+        int f = e - nxs;
+        if (f < (9 * NP) * (BX + 2)) {
+          const int w = BX + 2;
+          pl = f / w;
+          arr = pl < 8 * NP ? 0 : 1;
+          if (arr == 1) pl -= 8 * NP;
+          by = bottom ? 0 : G::HB - 1;
+          bx = (arr == 0 ? G::HXM : G::HXR) - 1 + f % w;
+        } else {
+          f -= (9 * NP) * (BX + 2);
+          const int w = BX + 2 * NC;
+          const int two = f % NC;
+          f /= NC;
+          pl = f / w;
+          arr = pl < NP ? 2 : 3;
+          if (arr == 3) pl -= NP;
+          by = bottom ? two : G::HBP - NC + two;
+          bx = G::HXR - NC + f % w;
+        }
+      }
+    };
+    // the patch's values, loaded before the wait (they do not depend on the
+    // stage; a thread's loads are all in flight at once)
+    uint32_t pv[PM];
+    if (PATCH && (patch_x || patch_y)) {  // CTA-uniform
+#pragma unroll
+      for (int m = 0; m < PM; ++m) {
+        const int e = tid + m * G::NTH;
+        if (e < nxs + nys) {
+          int arr, pl, bx, by;
+          entry(e, arr, pl, bx, by);
+          const int ox = arr == 0 ? G::HXM : (arr == 3 ? G::UOX : G::HXR);
+          const int oy = arr < 2 ? 1 : G::RY;
+          const size_t q = (size_t)pl * a.V +
+                           (size_t)wrap(y0 - oy + by, ny) * nx + wrap(x0 - ox + bx, nx);
+          const void *src = arr == 0 ? (const void *)(a.hm_in + q)
+                            : arr == 1 ? (const void *)(a.h0_in + q)
+                            : arr == 2 ? (const void *)(a.pp_in + q)
+                                       : (const void *)(a.u_in + q);
+          pv[m] = arr == 0 ? (uint32_t)__ldg((const unsigned short *)src)
+                           : __ldg((const unsigned int *)src);
+        }
+      }
+    }
+    // A thread whose wait gave up still runs the phi sums below (on stale
+    // shared data, harmlessly); the barrier after them makes the decision
+    // to stop the same for the whole CTA.
+    const bool ok = mbar_wait(bar + (j % S), (uint32_t)((j / S) & 1));
+    if (PATCH && (patch_x || patch_y)) {  // the stage has landed: patch it
+#pragma unroll
+      for (int m = 0; m < PM; ++m) {
+        const int e = tid + m * G::NTH;
+        if (e < nxs + nys) {
+          int arr, pl, bx, by;
+          entry(e, arr, pl, bx, by);
+          if (arr == 0) {
+            ((unsigned short *)stw)[(pl * G::HB + by) * G::WM + bx] = (unsigned short)pv[m];
+          } else if (arr == 1) {
+            ((uint32_t *)(stw + St::HM))[(pl * G::HB + by) * G::WR + bx] = pv[m];
+          } else if (arr == 2) {
+            ((uint32_t *)(stw + St::HM + St::H0))[(pl * G::HBP + by) * G::WR + bx] = pv[m];
+          } else {
+            ((uint32_t *)(stw + St::HM + St::H0 + St::PP + St::GM))[(pl * G::UH + by) * G::UW + bx] =
+                pv[m];
+          }
+        }
+      }
+      __syncthreads();
+    }
+
     // 16-bit forms: u(t-1) and phi(t-1) of the node that slot k of node
     // (xn, yn) was streamed from; (cb, rb) is the node's position in the
-    // u(t-1) and phi(t-1) boxes. Sources that wrap around the grid come from
-    // global memory.
-    // Tiles whose two-node neighbourhood lies inside the grid (no wrap, no
-    // wall) find every source in the boxes at a fixed offset.
-    const bool inner = x0 >= 2 && x0 + BX + 2 <= nx && y0 >= 2 && y0 + TBY + 2 <= ny;
+    // u(t-1) and phi(t-1) boxes (of the node itself behind a wall).
+    // WHOLE: always in the boxes. Otherwise tiles whose two-node
+    // neighbourhood lies inside the grid find every source in the boxes at
+    // a fixed offset, others read sources that wrap from global memory.
+    const bool inner = PATCH || (x0 >= 2 && x0 + BX + 2 <= nx && y0 >= 2 && y0 + TBY + 2 <= ny);
     auto source = [&](int k, int xn, int yn, int cb, int rb, T &sux, T &suy,
                       T &spr, T *sph) {
-      if (inner) {
-        const int o = (rb - cy_of(k)) * G::UW + cb - cx_of(k);
-        sux = sup[o];
-        suy = sup[G::UH * G::UW + o];
-        spr = sup[2 * G::UH * G::UW + o];
-#pragma unroll
-        for (int i = 0; i < NP; ++i)
-          sph[i] = spp[(i * G::HBP + rb - cy_of(k)) * G::WR + cb - cx_of(k)];
-        return;
+      int r = rb - cy_of(k), c = cb - cx_of(k);
+      bool box = true;
+      if (!PATCH && !inner) {
+        int sx = xn - cx_of(k), sy = yn - cy_of(k);
+        if (WALL && (sy < 0 || sy >= ny)) {
+          sx = xn; sy = yn; c = cb; r = rb;
+        }
+        box = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
+      } else if (WALL) {
+        const int sy = yn - cy_of(k);
+        if (sy < 0 || sy >= ny) { c = cb; r = rb; }
       }
-      int sx = xn - cx_of(k), sy = yn - cy_of(k);
-      int c = cb - cx_of(k), r = rb - cy_of(k);
-      if (WALL && (sy < 0 || sy >= ny)) {
-        sx = xn; sy = yn; c = cb; r = rb;
-      }
-      if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) {
+      if (box) {
         sux = sup[r * G::UW + c];
         suy = sup[(G::UH + r) * G::UW + c];
         spr = sup[(2 * G::UH + r) * G::UW + c];
@@ -1165,26 +1279,9 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
       }
     };
     const T s3h = T(3) * a.sh_st, srg = a.rho_base * a.sg_st, s3g = T(3) * a.sg_st;
-    // A thread whose wait gave up still runs the phi sums below (on stale
-    // shared data, harmlessly); the barrier after them makes the decision
-    // to stop the same for the whole CTA.
-    const bool ok = mbar_wait(bar + (j % S), (uint32_t)((j / S) & 1));
 
-    // phi on the tile and its ring. A position whose node lies inside the
-    // array without wrapping reads the staged box; others read global memory.
-    // phi at a position of a staged wrap box: planes `pm` / `pr` apart,
-    // the position at offsets om / orr in them, into sphi[.][o]
-    auto wrap_phi = [&](const Sm *hmb, const T *h0b, const T *ppb, int pm, int pr,
-                        int om, int orr, int o) {
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T mov[8], e;
-#pragma unroll
-        for (int k = 1; k < 9; ++k) mov[k - 1] = to_T(hmb[(i * 8 + k - 1) * pm + om]);
-        sphi[i * PL + o] = node_phi<P>(h0b[i * pr + orr], mov, ppb[i * pr + orr], e, a.sh_ld);
-      }
-    };
-    // (the result goes to sphi row `out_row`, by default the box row)
+    // phi on the tile and its ring, from the staged boxes (the result goes
+    // to sphi row `out_row`, by default the box row).
     auto box_phi = [&](int bxm, int bxr, int by, T *err, int out_row = -1) {
       T mv[NP][8];
 #pragma unroll
@@ -1256,26 +1353,39 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
       ring_pos_1<TBY>(tid, lx, ly);
       const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
       const bool inx = rx >= 0 && rx < nx, iny = ry >= 0 && ry < ny;
-      if (inx && iny) {
+      if (PATCH) {
+        // a wall's ghost row is the adjacent row of the box
+        const int by = WALL ? wrap_y<WALL>(ry, ny) - y0 + 1 : ly;
+        box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, by, nullptr, ly);
+      } else if (inx && iny) {
         box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, ly, nullptr);
       } else if constexpr (G::WRAP) {
         // staged wrapped column or row, a wall's ghost row from the box, or
         // (corners, ragged tails) global memory
         const int wx = halo_x(x0), wy = halo_y(y0);
         const unsigned char *w = st + St::BASE;
+        auto wrap_phi = [&](const Sm *hmb, const T *h0b, const T *ppb, int pm, int pr,
+                            int om, int orr) {
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            T mov[8], e;
+#pragma unroll
+            for (int k = 1; k < 9; ++k) mov[k - 1] = to_T(hmb[(i * 8 + k - 1) * pm + om]);
+            sphi[i * PL + ly * SW + lx] =
+                node_phi<P>(h0b[i * pr + orr], mov, ppb[i * pr + orr], e, a.sh_ld);
+          }
+        };
         if (iny && ((rx < 0 && wx == 1) || (rx >= nx && wx == 2))) {
           const int c = rx < 0 ? G::HXR - 1 : 0;
-          wrap_phi((const Sm *)w, (const T *)(w + St::XHM),
-                   (const T *)(w + St::XHM + St::XH0), G::HB * G::HXM,
-                   G::HB * G::HXR, ly * G::HXM + c, ly * G::HXR + c, ly * SW + lx);
+          wrap_phi((const Sm *)w, (const T *)(w + St::XHM), (const T *)(w + St::XHM + St::XH0),
+                   G::HB * G::HXM, G::HB * G::HXR, ly * G::HXM + c, ly * G::HXR + c);
         } else if (inx && WALL) {
-          box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, wrap_y<WALL>(ry, ny) - y0 + 1,
-                  nullptr, ly);
+          box_phi(lx - 1 + G::HXM, lx - 1 + G::HXR, wrap_y<WALL>(ry, ny) - y0 + 1, nullptr,
+                  ly);
         } else if (inx && ((ry < 0 && wy == 1) || (ry >= ny && wy == 2))) {
           w += St::XHM + St::XH0 + St::XPP;
-          wrap_phi((const Sm *)w, (const T *)(w + St::YHM),
-                   (const T *)(w + St::YHM + St::YH0), G::WM, G::WR,
-                   lx - 1 + G::HXM, lx - 1 + G::HXR, ly * SW + lx);
+          wrap_phi((const Sm *)w, (const T *)(w + St::YHM), (const T *)(w + St::YHM + St::YH0),
+                   G::WM, G::WR, lx - 1 + G::HXM, lx - 1 + G::HXR);
         } else {
           phi_global<P, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
                                   ly * SW + lx);
@@ -1480,25 +1590,26 @@ cudaError_t launch_tile_t(const Consts &c, const Grid &g, int cur, int mode,
   if constexpr (P != LBM_FP64 && !NU) {
     if (mode == MODE_STEP && g.use_tma && g.grad_scheme == 0) {
       typedef TmaStage<P, NP> St;
-      static int max_ctas = 0;  // per instantiation: resident CTAs on the GPU
-      if (max_ctas == 0) {
+      constexpr int TBY = TmaGeom<P>::TBY;
+      const bool whole = g.nx % BX == 0 && g.ny % TBY == 0 && g.nx > BX && g.ny > TBY;
+      auto kern = whole ? tile_kernel_tma<P, NP, WALL, true> : tile_kernel_tma<P, NP, WALL, false>;
+      static int max_ctas[2] = {0, 0};  // per instantiation: resident CTAs on the GPU
+      int &mc = max_ctas[whole ? 1 : 0];
+      if (mc == 0) {
         cudaError_t e = cudaFuncSetAttribute(
-            tile_kernel_tma<P, NP, WALL>,
-            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)St::SMEM);
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)St::SMEM);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, tile_kernel_tma<P, NP, WALL>, TmaGeom<P>::NTH, St::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TmaGeom<P>::NTH,
+                                                          St::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        max_ctas = (per_sm > 0 ? per_sm : 1) * sms;
+        mc = (per_sm > 0 ? per_sm : 1) * sms;
       }
-      constexpr int TBY = TmaGeom<P>::TBY;
       const int ntx = tiles_x(g.nx), ntiles = ntx * ((g.ny + TBY - 1) / TBY);
-      const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-      tile_kernel_tma<P, NP, WALL><<<grid, dim3(BX, TBY), St::SMEM, s>>>(
-          a, *(const TmaMaps *)&g.tma[cur], ntx, ntiles);
+      const int grid = ntiles < mc ? ntiles : mc;
+      kern<<<grid, dim3(BX, TBY), St::SMEM, s>>>(a, *(const TmaMaps *)&g.tma[cur], ntx, ntiles);
       return cudaGetLastError();
     }
   }
