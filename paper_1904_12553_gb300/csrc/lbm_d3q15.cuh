@@ -771,10 +771,27 @@ template <int P, int NP> struct March3Stage {
   static constexpr size_t PP = H0;
   static constexpr size_t GM = al((size_t)14 * MY3 * MX3 * sizeof(T));
   static constexpr size_t UP = al((size_t)3 * MY3 * MX3 * sizeof(T));
-  static constexpr size_t BYTES = HM + H0 + PP + GM + UP;
+  static constexpr size_t BASE = HM + H0 + PP + GM + UP;  // offset of the wrap boxes
   static constexpr uint32_t TX =
       (uint32_t)(((size_t)NP * 16 * BH * BW + (size_t)17 * MY3 * MX3) * sizeof(T));
   static constexpr size_t WIN = (size_t)3 * NP * (MX3 + 2) * (MY3 + 2) * sizeof(T);
+  // The ring column (x) and row (y) that wrap around a periodic grid are
+  // staged too, for edge columns: 16 bytes of columns at the far x edge over
+  // the box height, and one row at the far y edge over the box width, of
+  // the h, d_0 and phi(t-1) arrays (16 NP planes). The row only where it
+  // fits beside the rest (N <= 3).
+  // (each box at a 128-byte boundary of shared memory, as TMA requires)
+  static constexpr size_t XHM = al((size_t)14 * NP * BH * HX * sizeof(T));
+  static constexpr size_t XH0 = al((size_t)NP * BH * HX * sizeof(T));
+  static constexpr size_t XW = XHM + 2 * XH0;
+  static constexpr size_t YHM = al((size_t)14 * NP * BW * sizeof(T));
+  static constexpr size_t YH0 = al((size_t)NP * BW * sizeof(T));
+  static constexpr size_t YW0 = YHM + 2 * YH0;
+  static constexpr bool WRAP_Y = 2 * (BASE + XW + YW0) + WIN + 16 <= 232448;
+  static constexpr size_t YW = WRAP_Y ? YW0 : 0;
+  static constexpr uint32_t XTX = (uint32_t)((size_t)16 * NP * BH * HX * sizeof(T));
+  static constexpr uint32_t YTX = (uint32_t)((size_t)16 * NP * BW * sizeof(T));
+  static constexpr size_t BYTES = BASE + XW + YW;
   static constexpr size_t SMEM = 2 * BYTES + WIN + 16;
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
@@ -810,32 +827,55 @@ __global__ void __launch_bounds__(MT3, 1)
   // stage and barrier of plane p >= zs; the barrier's k-th completion
   // (parity k & 1) is the k-th plane loaded into that stage
   auto stage = [&](int p) { return smem_t3 + ((p - zs) & 1) * St::BYTES; };
+  // which wrapped halo column (1: x = -1 from nx - 4 .. nx - 1; 2: x = nx
+  // from 0 .. 3) and row (1: y = -1 from ny - 1; 2: y = ny from 0; none with
+  // walls, whose ghost rows repeat a row of the box) this column stages
+  const int wx = x0 == 0 ? 1 : (x0 + MX3 == nx ? 2 : 0);
+  const int wy = (!St::WRAP_Y || WALL) ? 0 : (y0 == 0 ? 1 : (y0 + MY3 == ny ? 2 : 0));
   auto issue = [&](int p) {  // thread 0
     unsigned char *st = stage(p);
     uint64_t *b = bar + ((p - zs) & 1);
     const int pz = wrap(p, nz);
-    mbar_expect_tx(b, St::TX);
+    mbar_expect_tx(b, St::TX + (wx ? St::XTX : 0u) + (wy ? St::YTX : 0u));
     tma_load_4d(st, &maps.hm, x0 - HX, y0 - 1, pz, 0, b);
     tma_load_4d(st + St::HM, &maps.h0, x0 - HX, y0 - 1, pz, 0, b);
     tma_load_4d(st + St::HM + St::H0, &maps.pp, x0 - HX, y0 - 1, pz, 0, b);
     tma_load_4d(st + St::HM + St::H0 + St::PP, &maps.gm, x0, y0, pz, 0, b);
     tma_load_4d(st + St::HM + St::H0 + St::PP + St::GM, &maps.up, x0, y0, pz, 0, b);
+    unsigned char *w = st + St::BASE;
+    if (wx) {  // planes h_1..14, d_0, phi(t-1) per phase: 14 NP, NP, NP
+      const int xs = wx == 1 ? nx - HX : 0;
+      tma_load_4d(w, &maps.hmx, xs, y0 - 1, pz, 0, b);
+      tma_load_4d(w + St::XHM, &maps.h0x, xs, y0 - 1, pz, 0, b);
+      tma_load_4d(w + St::XHM + St::XH0, &maps.ppx, xs, y0 - 1, pz, 0, b);
+    }
+    if (wy) {
+      const int ys = wy == 1 ? ny - 1 : 0;
+      w += St::XW;
+      tma_load_4d(w, &maps.hmy, x0 - HX, ys, pz, 0, b);
+      tma_load_4d(w + St::YHM, &maps.h0y, x0 - HX, ys, pz, 0, b);
+      tma_load_4d(w + St::YHM + St::YH0, &maps.ppy, x0 - HX, ys, pz, 0, b);
+    }
   };
   auto wait = [&](int p) {
     return mbar_wait(bar + ((p - zs) & 1), (uint32_t)(((p - zs) >> 1) & 1));
   };
-  // phi at box position (bx, by) of a stage, summed as in node_phis3
-  auto box_phis = [&](const unsigned char *st, int bx, int by, T(&phv)[NP]) {
-    const T *hm = (const T *)st, *h0 = (const T *)(st + St::HM),
-            *pp = (const T *)(st + St::HM + St::H0);
+  // phi from staged planes, summed as in node_phis3: planes `pst` apart in
+  // the h (14 NP), d_0 (NP) and phi(t-1) (NP) arrays that start at hm, h0,
+  // pp, the position at offset o in each plane
+  auto sum_phis = [&](const T *hm, const T *h0, const T *pp, int pst, int o, T(&phv)[NP]) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      T small = h0[(i * BH + by) * BW + bx];
+      T small = h0[i * pst + o];
 #pragma unroll
-      for (int k = 1; k < 15; ++k)
-        small = __fadd_rn_T(small, hm[((i * 14 + k - 1) * BH + by) * BW + bx]);
-      phv[i] = __fadd_rn(pp[(i * BH + by) * BW + bx], small);
+      for (int k = 1; k < 15; ++k) small = __fadd_rn_T(small, hm[(i * 14 + k - 1) * pst + o]);
+      phv[i] = __fadd_rn(pp[i * pst + o], small);
     }
+  };
+  // phi at box position (bx, by) of a stage
+  auto box_phis = [&](const unsigned char *st, int bx, int by, T(&phv)[NP]) {
+    sum_phis((const T *)st, (const T *)(st + St::HM), (const T *)(st + St::HM + St::H0),
+             BH * BW, by * BW + bx, phv);
   };
   // phi of plane z on the tile and its xy ring, from global memory (plane
   // zs - 1) or from the stage (planes zs .. ze)
@@ -860,8 +900,20 @@ __global__ void __launch_bounds__(MT3, 1)
       ring_pos_1<MY3>(tid, lx, ly);
       const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
       T phv[NP];
-      if (staged && X >= 0 && X < nx && Y >= 0 && Y < ny) {
+      const bool inx = X >= 0 && X < nx, iny = Y >= 0 && Y < ny;
+      const unsigned char *wb = stage(z) + St::BASE;
+      if (staged && inx && iny) {
         box_phis(stage(z), lx - 1 + HX, ly, phv);
+      } else if (staged && iny && ((X < 0 && wx == 1) || (X >= nx && wx == 2))) {
+        // the staged wrapped column
+        sum_phis((const T *)wb, (const T *)(wb + St::XHM), (const T *)(wb + St::XHM + St::XH0),
+                 BH * HX, ly * HX + (X < 0 ? HX - 1 : 0), phv);
+      } else if (staged && inx && WALL) {  // a wall's ghost row: the adjacent row
+        box_phis(stage(z), lx - 1 + HX, wrap_y<WALL>(Y, ny) - y0 + 1, phv);
+      } else if (staged && inx && ((Y < 0 && wy == 1) || (Y >= ny && wy == 2))) {
+        const unsigned char *yw = wb + St::XW;  // the staged wrapped row
+        sum_phis((const T *)yw, (const T *)(yw + St::YHM), (const T *)(yw + St::YHM + St::YH0),
+                 BW, lx - 1 + HX, phv);
       } else {
         const int rx = wrap(X, nx), ry = wrap_y<WALL>(Y, ny);
         node_phis3<P, NP, WALL>(a, nz, rx, ry, zz, ((size_t)zz * ny + ry) * nx + rx, phv);
@@ -1144,7 +1196,14 @@ bool encode_tma3_p(const Consts &c, Grid &g, EncodeTiledFn enc) {
                       enc4(&m.h0, g.h0[b], NP, S1::BW, S1::BH) &&
                       enc4(&m.pp, g.phi_prev[b], NP, S1::BW, S1::BH) &&
                       enc4(&m.gm, g.gm[b], 14, MX3, MY3) &&
-                      enc4(&m.up, g.u_prev[b], 3, MX3, MY3);
+                      enc4(&m.up, g.u_prev[b], 3, MX3, MY3) &&
+                      // the wrapped halo column and row
+                      enc4(&m.hmx, g.hm[b], 14 * NP, S1::HX, S1::BH) &&
+                      enc4(&m.h0x, g.h0[b], NP, S1::HX, S1::BH) &&
+                      enc4(&m.ppx, g.phi_prev[b], NP, S1::HX, S1::BH) &&
+                      enc4(&m.hmy, g.hm[b], 14 * NP, S1::BW, 1) &&
+                      enc4(&m.h0y, g.h0[b], NP, S1::BW, 1) &&
+                      enc4(&m.ppy, g.phi_prev[b], NP, S1::BW, 1);
       if (!ok) return false;
     }
     return true;
