@@ -80,7 +80,7 @@ def test_d3q15_fp64_short_runs(N, shape, wall, nu):
 MARCH = [(N, prec, shape, wall)
          for N in (2, 3, 4, 5)
          for prec in ("fp64", "fp32", "fp16")
-         for shape in ((40, 17, 23), (8, 8, 1), (64, 24, 70))
+         for shape in ((40, 17, 23), (8, 8, 1), (64, 24, 70), (32, 16, 12))
          for wall in (0, 1)]
 
 

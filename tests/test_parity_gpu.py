@@ -324,13 +324,17 @@ def test_full_size_n5_2048_fp32():
 # ---------------------------------------------------------------------------
 # The TMA-pipelined step kernel against the generic tile kernel: same step,
 # same arithmetic, for every N, boundary, storage form, tiles fewer and more
-# than the SMs, ragged tails in y and periodic edges in both directions.
+# than the SMs, ragged tails in y and periodic edges in both directions. The
+# grids of whole 32 x 8 tiles (64 x 48, 96 x 40, 64 x 16: every tile an edge
+# tile in y) run the branch-free kernel whose edge tiles' boxes are made
+# periodic (16-bit) or carry staged wrapped halos (FP32); the others the
+# general one.
 # ---------------------------------------------------------------------------
 
 PIPE = [(N, prec, nx, ny, wall)
         for N in (2, 3, 4, 5)
         for prec in ("fp32", "bf16", "fp16")
-        for (nx, ny) in ((64, 48), (96, 45), (8, 8), (520, 300))
+        for (nx, ny) in ((64, 48), (96, 40), (64, 16), (96, 45), (8, 8), (520, 300))
         for wall in (0, 1)]
 
 
