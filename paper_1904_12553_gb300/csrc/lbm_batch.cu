@@ -168,9 +168,14 @@ constexpr size_t kStageStride = BSt::BYTES + ((kArgsBytes + 127) & ~(size_t)127)
 constexpr size_t kBatchSmem = BSt::S * kStageStride + 2 * BSt::SPHI + 64;
 static_assert(kBatchSmem <= 232448, "shared memory per CTA");
 
-// Item descriptor of the pipelined kernel.
+// Item descriptor of the pipelined kernel: case, tile origin, class 2 (N - 1)
+// + walls; for a tile on the edge of a periodic case, which wrapped halo
+// column (wx: 1 the column x = -1, staged from x = nx - 4 .. nx - 1; 2 the
+// column x = nx, from 0 .. 3) and row (wy: 1 the row y = -1, from ny - 1; 2
+// the row y = ny, from 0) are staged with it, and their first source column
+// and row (xs, ys).
 struct alignas(16) TmaItem {
-  int c, x0, y0, cls;  // case, tile origin, 2 (N - 1) + walls
+  int c, x0, y0, cls, wx, wy, xs, ys;
 };
 
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
@@ -190,14 +195,29 @@ template <int NP>
 __device__ __forceinline__ void batch_issue_np(unsigned char *st, uint64_t *b,
                                                const TmaMaps *m,
                                                const KArgs<LBM_FP32> *args,
-                                               int x0, int y0) {
+                                               const TmaItem &d) {
   typedef TmaStage<LBM_FP32, NP> St;
-  mbar_expect_tx(b, St::TX + (uint32_t)kArgsBytes);
+  const int x0 = d.x0, y0 = d.y0;
+  mbar_expect_tx(b, St::TX + (uint32_t)kArgsBytes + (d.wx ? St::XTX : 0u) +
+                        (d.wy ? St::YTX : 0u));
   tma_load_3d(st, &m->hm, x0 - BG::HXM, y0 - 1, 0, b);
   tma_load_3d(st + St::HM, &m->h0, x0 - BG::HXR, y0 - 1, 0, b);
   tma_load_3d(st + St::HM + St::H0, &m->pp, x0 - BG::HXR, y0 - 1, 0, b);
   tma_load_3d(st + St::HM + St::H0 + St::PP, &m->gm, x0, y0, 0, b);
   tma_load_3d(st + St::HM + St::H0 + St::PP + St::GM, &m->up, x0, y0, 0, b);
+  // the wrapped halo column and row of an edge tile
+  unsigned char *w = st + St::BASE;
+  if (d.wx) {
+    tma_load_3d(w, &m->hmx, d.xs, y0 - 1, 0, b);
+    tma_load_3d(w + St::XHM, &m->h0x, d.xs, y0 - 1, 0, b);
+    tma_load_3d(w + St::XHM + St::XH0, &m->ppx, d.xs, y0 - 1, 0, b);
+  }
+  if (d.wy) {
+    w += St::XHM + St::XH0 + St::XPP;
+    tma_load_3d(w, &m->hmy, x0 - BG::HXM, d.ys, 0, b);
+    tma_load_3d(w + St::YHM, &m->h0y, x0 - BG::HXR, d.ys, 0, b);
+    tma_load_3d(w + St::YHM + St::YH0, &m->ppy, x0 - BG::HXR, d.ys, 0, b);
+  }
   bulk_load(st + BSt::BYTES, args, (uint32_t)kArgsBytes, b);
 }
 
@@ -214,7 +234,7 @@ template <int NP, bool WALL>
 __device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
                                               const unsigned char *st,
                                               float *sphi, int x0, int y0,
-                                              TileRegs &r) {
+                                              int wx, int wy, TileRegs &r) {
   typedef float T;
   typedef typename Prec<LBM_FP32>::Sm Sm;
   typedef TmaStage<LBM_FP32, NP> St;
@@ -244,24 +264,48 @@ __device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
     phi_global<LBM_FP32, NP, WALL>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                              (ty + 1) * SW + tx + 1);
   }
+  // The ring's positions go to warps 1..3 (threads 32 .. 32 + NRING - 1):
+  // warp 0 holds the thread that fetches the next item and issues its
+  // copies, which then overlaps the ring sums instead of adding to them.
   constexpr int NRING = SW * SH - BX * TBY;
-  if (tid < NRING) {
+  static_assert(32 + NRING <= BX * TBY, "one ring position per thread");
+  if (tid >= 32 && tid < 32 + NRING) {
     int lx, ly;
-    ring_pos_1<TBY>(tid, lx, ly);
+    ring_pos_1<TBY>(tid - 32, lx, ly);
     const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
-    if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) {
-      const int bxm = lx - 1 + BG::HXM, bxr = lx - 1 + BG::HXR;
+    const bool inx = rx >= 0 && rx < nx, iny = ry >= 0 && ry < ny;
+    // phi of one ring position from staged populations: hmb, h0b, ppb are
+    // the moving, rest and phi(t-1) planes with plane strides pm, pr; om,
+    // orr the position's offset in them
+    auto staged_phi = [&](const Sm *hmb, const T *h0b, const T *ppb, int pm, int pr,
+                          int om, int orr) {
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         T mov[8], e;
 #pragma unroll
-        for (int k = 1; k < 9; ++k)
-          mov[k - 1] = to_T(shm[((i * 8 + k - 1) * BG::HB + ly) * BG::WM + bxm]);
-        sphi[i * PL + ly * SW + lx] = node_phi<LBM_FP32>(
-            sh0[(i * BG::HB + ly) * BG::WR + bxr], mov,
-            spp[(i * BG::HB + ly) * BG::WR + bxr], e, a.sh_ld);
+        for (int k = 1; k < 9; ++k) mov[k - 1] = to_T(hmb[(i * 8 + k - 1) * pm + om]);
+        sphi[i * PL + ly * SW + lx] =
+            node_phi<LBM_FP32>(h0b[i * pr + orr], mov, ppb[i * pr + orr], e, a.sh_ld);
       }
+    };
+    const unsigned char *w = st + St::BASE;
+    if (inx && (iny || WALL)) {
+      // in the box; a wall's ghost row is the adjacent row of the box
+      const int by = WALL ? wrap_y<WALL>(ry, ny) - y0 + 1 : ly;
+      staged_phi(shm, sh0, spp, BG::HB * BG::WM, BG::HB * BG::WR,
+                 by * BG::WM + lx - 1 + BG::HXM, by * BG::WR + lx - 1 + BG::HXR);
+    } else if (iny && ((rx < 0 && wx == 1) || (rx >= nx && wx == 2))) {
+      // the staged wrapped column
+      const int c = rx < 0 ? BG::HXR - 1 : 0;
+      staged_phi((const Sm *)w, (const T *)(w + St::XHM), (const T *)(w + St::XHM + St::XH0),
+                 BG::HB * BG::HXM, BG::HB * BG::HXR, ly * BG::HXM + c, ly * BG::HXR + c);
+    } else if (inx && ((ry < 0 && wy == 1) || (ry >= ny && wy == 2))) {
+      // the staged wrapped row
+      w += St::XHM + St::XH0 + St::XPP;
+      staged_phi((const Sm *)w, (const T *)(w + St::YHM), (const T *)(w + St::YHM + St::YH0),
+                 BG::WM, BG::WR, lx - 1 + BG::HXM, lx - 1 + BG::HXR);
     } else {
+      // corners and ragged tails
       phi_global<LBM_FP32, NP, WALL>(a, wrap(rx, nx), wrap_y<WALL>(ry, ny), sphi, PL,
                                ly * SW + lx);
     }
@@ -328,7 +372,7 @@ __global__ void __launch_bounds__(BG::NTH, 1)
     ++k;
     return item;
   };
-  const TmaItem none = {-1, 0, 0, 0};
+  const TmaItem none = {-1, 0, 0, 0, 0, 0, 0, 0};
   TmaItem d_next = none;
   int i_after = nitems;
   auto issue = [&](int j) {  // thread 0: the CTA's j-th item into stage j % S
@@ -347,15 +391,21 @@ __global__ void __launch_bounds__(BG::NTH, 1)
       tensormap_acquire(&m->pp);
       tensormap_acquire(&m->gm);
       tensormap_acquire(&m->up);
+      tensormap_acquire(&m->hmx);
+      tensormap_acquire(&m->h0x);
+      tensormap_acquire(&m->ppx);
+      tensormap_acquire(&m->hmy);
+      tensormap_acquire(&m->h0y);
+      tensormap_acquire(&m->ppy);
       fenced = d.c;
     }
     unsigned char *st = smem + slot * kStageStride;
     const KArgs<LBM_FP32> *args = &cases[d.c].a[cur];
     switch (d.cls >> 1) {
-      case 1: batch_issue_np<1>(st, bar + slot, m, args, d.x0, d.y0); break;
-      case 2: batch_issue_np<2>(st, bar + slot, m, args, d.x0, d.y0); break;
-      case 3: batch_issue_np<3>(st, bar + slot, m, args, d.x0, d.y0); break;
-      default: batch_issue_np<4>(st, bar + slot, m, args, d.x0, d.y0); break;
+      case 1: batch_issue_np<1>(st, bar + slot, m, args, d); break;
+      case 2: batch_issue_np<2>(st, bar + slot, m, args, d); break;
+      case 3: batch_issue_np<3>(st, bar + slot, m, args, d); break;
+      default: batch_issue_np<4>(st, bar + slot, m, args, d); break;
     }
     ++issued;
   };
@@ -386,14 +436,14 @@ __global__ void __launch_bounds__(BG::NTH, 1)
     const int x0 = d.x0, y0 = d.y0;
     TileRegs r;
     switch (d.cls) {
-      case 2: batch_tma_phi<1, false>(sa, st, sphi, x0, y0, r); break;
-      case 3: batch_tma_phi<1, true>(sa, st, sphi, x0, y0, r); break;
-      case 4: batch_tma_phi<2, false>(sa, st, sphi, x0, y0, r); break;
-      case 5: batch_tma_phi<2, true>(sa, st, sphi, x0, y0, r); break;
-      case 6: batch_tma_phi<3, false>(sa, st, sphi, x0, y0, r); break;
-      case 7: batch_tma_phi<3, true>(sa, st, sphi, x0, y0, r); break;
-      case 8: batch_tma_phi<4, false>(sa, st, sphi, x0, y0, r); break;
-      case 9: batch_tma_phi<4, true>(sa, st, sphi, x0, y0, r); break;
+      case 2: batch_tma_phi<1, false>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 3: batch_tma_phi<1, true>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 4: batch_tma_phi<2, false>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 5: batch_tma_phi<2, true>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 6: batch_tma_phi<3, false>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 7: batch_tma_phi<3, true>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 8: batch_tma_phi<4, false>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
+      case 9: batch_tma_phi<4, true>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
     }
     // A thread whose wait gave up ran the phi sums on stale shared data
     // (harmlessly); this barrier makes the decision to stop CTA-wide.
@@ -581,8 +631,13 @@ lbm_status build_schedule(lbm_nphase_batch_t *b, lbm_nphase_batch_schedule s) {
     for (size_t i = 0; i < items.size(); ++i) {
       const lbm_nphase_t *h = b->cases[items[i].x];
       const int ntx = lbm::tiles_x(h->prm.nx), t = items[i].y;
-      titems[i] = {items[i].x, (t % ntx) * lbm::BX, (t / ntx) * tby,
-                   h->k.NP * 2 + (h->wall ? 1 : 0)};
+      const int x0 = (t % ntx) * lbm::BX, y0 = (t / ntx) * tby;
+      const int nx = h->prm.nx, ny = h->prm.ny;
+      // wrapped halo column / row staged with an edge tile (periodic axes)
+      const int wx = x0 == 0 ? 1 : (x0 + lbm::BX == nx ? 2 : 0);
+      const int wy = h->wall ? 0 : (y0 == 0 ? 1 : (y0 + tby == ny ? 2 : 0));
+      titems[i] = {items[i].x, x0, y0, h->k.NP * 2 + (h->wall ? 1 : 0), wx, wy,
+                   wx == 1 ? nx - lbm::TmaGeom<LBM_FP32>::HXR : 0, wy == 1 ? ny - 1 : 0};
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->d_titems, titems.data(),

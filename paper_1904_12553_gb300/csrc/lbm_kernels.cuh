@@ -1346,11 +1346,13 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
       phi_global<P, NP, WALL>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                         (ty + 1) * SW + tx + 1);
     }
+    // ring positions on warps 1..3 (threads 32 .. 32 + NRING - 1): warp 0
+    // holds the thread that issues the stage refills
     constexpr int NRING = SW * SH - BX * TBY;
-    static_assert(NRING <= G::NTH, "one ring position per thread");
-    if (tid < NRING) {
+    static_assert(32 + NRING <= G::NTH, "one ring position per thread");
+    if (tid >= 32 && tid < 32 + NRING) {
       int lx, ly;
-      ring_pos_1<TBY>(tid, lx, ly);
+      ring_pos_1<TBY>(tid - 32, lx, ly);
       const int rx = x0 - 1 + lx, ry = y0 - 1 + ly;
       const bool inx = rx >= 0 && rx < nx, iny = ry >= 0 && ry < ny;
       if (PATCH) {
