@@ -893,11 +893,13 @@ __global__ void __launch_bounds__(MT3, 1)
 #pragma unroll
       for (int i = 0; i < NP; ++i) w[i][(ty + 1) * SW + tx + 1] = phv[i];
     }
+    // ring positions on warps 1..3 (threads 32 .. 32 + NRING - 1): warp 0
+    // holds the thread that issues the plane copies
     constexpr int NRING = PL - MT3;
-    static_assert(NRING <= MT3, "one ring position per thread");
-    if (tid < NRING) {
+    static_assert(32 + NRING <= MT3, "one ring position per thread");
+    if (tid >= 32 && tid < 32 + NRING) {
       int lx, ly;
-      ring_pos_1<MY3>(tid, lx, ly);
+      ring_pos_1<MY3>(tid - 32, lx, ly);
       const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
       T phv[NP];
       const bool inx = X >= 0 && X < nx, iny = Y >= 0 && Y < ny;
