@@ -227,7 +227,7 @@ __device__ __forceinline__ void batch_issue_np(unsigned char *st, uint64_t *b,
 // shared by every (N - 1, walls) variant, so that the variants do not add up
 // their live registers across the barrier.
 struct TileRegs {
-  float hreg[4][9], perr[4], pp[4], g[9];
+  float hreg[4][9], perr[4], pp[4], g[9], up[2];
 };
 
 template <int NP, bool WALL>
@@ -260,6 +260,10 @@ __device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
     }
 #pragma unroll
     for (int k = 1; k < 9; ++k) r.g[k] = to_T(sgm[((k - 1) * TBY + ty) * BX + tx]);
+    // u(t-1): the stage is not read after the tile's barrier
+    const T *sup = (const T *)(st + St::HM + St::H0 + St::PP + St::GM);
+    r.up[0] = sup[ty * BX + tx];
+    r.up[1] = sup[(TBY + ty) * BX + tx];
   } else {
     phi_global<LBM_FP32, NP, WALL>(a, wrap(gx, nx), wrap_y<WALL>(gy, ny), sphi, PL,
                              (ty + 1) * SW + tx + 1);
@@ -314,16 +318,13 @@ __device__ __forceinline__ void batch_tma_phi(const KArgs<LBM_FP32> &a,
 
 template <int NP, bool WALL>
 __device__ __forceinline__ void batch_tma_collide(const KArgs<LBM_FP32> &a,
-                                                  const unsigned char *st,
                                                   const float *sphi, int x0,
                                                   int y0, TileRegs &r) {
-  typedef TmaStage<LBM_FP32, NP> St;
   constexpr int TBY = BG::TBY;
   constexpr int SW = BX + 2, PL = SW * (TBY + 2);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int gx = x0 + tx, gy = y0 + ty;
   if (gx >= a.nx || gy >= a.ny) return;
-  const float *sup = (const float *)(st + St::HM + St::H0 + St::PP + St::GM);
   float hreg[NP][9], perr[NP], pp[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
@@ -335,9 +336,8 @@ __device__ __forceinline__ void batch_tma_collide(const KArgs<LBM_FP32> &a,
   NodeMac<LBM_FP32, NP> m;
   node_macros<LBM_FP32, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1,
                                           tx + 1, 0, 0, r.g, m);
-  collide_stream<LBM_FP32, NP, false, WALL>(a, m, hreg, perr, r.g, pp,
-                                            sup[ty * BX + tx],
-                                            sup[(TBY + ty) * BX + tx], gx, gy);
+  collide_stream<LBM_FP32, NP, false, WALL>(a, m, hreg, perr, r.g, pp, r.up[0],
+                                            r.up[1], gx, gy);
 }
 
 __global__ void __launch_bounds__(BG::NTH, 1)
@@ -446,26 +446,28 @@ __global__ void __launch_bounds__(BG::NTH, 1)
       case 9: batch_tma_phi<4, true>(sa, st, sphi, x0, y0, d.wx, d.wy, r); break;
     }
     // A thread whose wait gave up ran the phi sums on stale shared data
-    // (harmlessly); this barrier makes the decision to stop CTA-wide.
+    // (harmlessly); this barrier makes the decision to stop CTA-wide. Past
+    // it no thread reads the stage (u(t-1) is in registers), so it is
+    // refilled at once; the phi tile is double-buffered, so this is the
+    // tile's only barrier (a thread at the next tile's barrier is done with
+    // this tile's phi tile).
     if (__syncthreads_or(!ok)) {
       failed_at = j;
       break;
     }
-    switch (d.cls) {
-      case 2: batch_tma_collide<1, false>(sa, st, sphi, x0, y0, r); break;
-      case 3: batch_tma_collide<1, true>(sa, st, sphi, x0, y0, r); break;
-      case 4: batch_tma_collide<2, false>(sa, st, sphi, x0, y0, r); break;
-      case 5: batch_tma_collide<2, true>(sa, st, sphi, x0, y0, r); break;
-      case 6: batch_tma_collide<3, false>(sa, st, sphi, x0, y0, r); break;
-      case 7: batch_tma_collide<3, true>(sa, st, sphi, x0, y0, r); break;
-      case 8: batch_tma_collide<4, false>(sa, st, sphi, x0, y0, r); break;
-      case 9: batch_tma_collide<4, true>(sa, st, sphi, x0, y0, r); break;
-    }
-    // Every thread is done with this stage: refill it.
-    __syncthreads();
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(j + S);
+    }
+    switch (d.cls) {
+      case 2: batch_tma_collide<1, false>(sa, sphi, x0, y0, r); break;
+      case 3: batch_tma_collide<1, true>(sa, sphi, x0, y0, r); break;
+      case 4: batch_tma_collide<2, false>(sa, sphi, x0, y0, r); break;
+      case 5: batch_tma_collide<2, true>(sa, sphi, x0, y0, r); break;
+      case 6: batch_tma_collide<3, false>(sa, sphi, x0, y0, r); break;
+      case 7: batch_tma_collide<3, true>(sa, sphi, x0, y0, r); break;
+      case 8: batch_tma_collide<4, false>(sa, sphi, x0, y0, r); break;
+      case 9: batch_tma_collide<4, true>(sa, sphi, x0, y0, r); break;
     }
   }
   if (failed_at >= 0) {

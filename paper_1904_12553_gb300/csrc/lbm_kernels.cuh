@@ -895,19 +895,22 @@ __global__ void __launch_bounds__(NT) tile_kernel(const KArgs<P> a) {
 // rows, ragged tails) are summed from global memory instead.
 // ---------------------------------------------------------------------------
 // Pipeline shape, chosen by timing the N=5 2048^2 step on GB300: 2 stages,
-// u(t-1) staged with the tile, two barriers per tile (the stage is refilled
-// right after the tile, so the next-but-one tile loads during a whole tile;
-// one phi tile suffices). FP32: 154 KB, one CTA per SM. 16-bit forms (their
-// populations decoded with phi(t-1) and u(t-1) of the source node: those two
-// boxes carry two halo rows): 111 KB and 128 registers, two CTAs per SM.
+// u(t-1) staged with the tile. FP32: two phi tiles and one barrier per tile
+// (the stage is refilled right after the tile's phi barrier, u(t-1) having
+// been read before it; with the wrapped halos staged this took the step
+// from 0.906 to 0.928 of the copy bandwidth), 185 KB, one CTA per SM.
+// 16-bit forms (their populations decoded with phi(t-1) and u(t-1) of the
+// source node: those two boxes carry two halo rows): one phi tile and two
+// barriers per tile (the stage refilled after the second), 111 KB and 128
+// registers, two CTAs per SM (a second phi tile would not leave room for two).
 // Measured and rejected:
-//  - FP32: a third stage (227 KB, ~28 KB of L1 left) -28%; one barrier per
-//    tile -23%; one stage with two CTAs per SM -15%; 32 x 12 tiles (384
+//  - FP32 (before the wrapped halos were staged): a third stage (227 KB,
+//    ~28 KB of L1 left) -28%; one barrier per tile with one phi tile -23%;
+//    one stage with two CTAs per SM -15%; 32 x 12 tiles (384
 //    threads, 225 KB) -30%; a stage without halo columns (wrapped ring
 //    columns from global memory, two CTAs per SM) -48%; g and u(t-1) loaded
 //    from global memory before the wait instead of staged -19% (a third
-//    stage on top, a further -6%); releasing the stage after the phi
-//    barrier (one barrier per tile) -9%; the ring's phi split over
+//    stage on top, a further -6%); the ring's phi split over
 //    (position, phase) pairs on all warps -1.5%; the stage refilled right
 //    after the phi barrier (two barriers kept) -9%; 32 x 4 tiles with two
 //    CTAs per SM (four stages in flight per SM) -27%; an L2 prefetch of the
@@ -1025,7 +1028,9 @@ template <int P, int NP> struct TmaStage {
       (uint32_t)((size_t)8 * NP * G::WM * sizeof(Sm) + (size_t)2 * NP * G::WR * sizeof(T));
   static constexpr size_t SPHI = al((size_t)NP * (G::TBY + 2) * (BX + 2) * sizeof(T));
   static constexpr int S = G::S;
-  static constexpr size_t SMEM = S * BYTES + SPHI + 64;
+  // FP32: two phi tiles (one barrier per tile, below); 16-bit forms: one
+  static constexpr int NPHI = G::WIDE ? 2 : 1;
+  static constexpr size_t SMEM = S * BYTES + NPHI * SPHI + 64;
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
@@ -1066,7 +1071,14 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
   constexpr int TBY = G::TBY;
   constexpr int SW = BX + 2, SH = TBY + 2, PL = SW * SH;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::SPHI);
+  uint64_t *bar = (uint64_t *)(smem + S * St::BYTES + St::NPHI * St::SPHI);
+  // FP32: the stage is not read after the tile's phi barrier (u(t-1) is
+  // loaded before it), so it is refilled right after that barrier, and with
+  // two phi tiles (tile j uses tile j & 1) that is the tile's only barrier:
+  // a thread at the next tile's barrier is done with this tile's phi tile.
+  // The 16-bit forms (one phi tile, to keep two CTAs per SM) refill after a
+  // second barrier at the end of the tile.
+  constexpr bool ONEB = St::NPHI == 2;
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int nx = a.nx, ny = a.ny;
@@ -1125,7 +1137,7 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
   for (int j = 0; j < nmine; ++j) {
     const int t = blockIdx.x + j * gridDim.x;
     const int x0 = (t % ntx) * BX, y0 = (t / ntx) * TBY;
-    T *sphi = (T *)(smem + S * St::BYTES);
+    T *sphi = (T *)(smem + S * St::BYTES + (ONEB ? (j & 1) * St::SPHI : 0));
     unsigned char *stw = smem + (j % S) * St::BYTES;
     const unsigned char *st = stw;
     const Sm *shm = (const Sm *)st;
@@ -1397,22 +1409,27 @@ __global__ void __launch_bounds__(TmaGeom<P>::NTH, TmaGeom<P>::WIDE ? 1 : 2)
                                 ly * SW + lx);
       }
     }
+    const T upx = sup[(ty + G::UOY) * G::UW + tx + G::UOX];
+    const T upy = sup[(G::UH + ty + G::UOY) * G::UW + tx + G::UOX];
     // phi of the tile and its ring complete (and the decision to stop
     // CTA-wide).
     if (__syncthreads_or(!ok)) {
       failed_at = j;
       break;
     }
+    if (ONEB && tid == 0 && issued < nmine) {  // the stage is free
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(issued);
+      ++issued;
+    }
 
     if (active) {
       NodeMac<P, NP> m;
       node_macros<P, NP, false, SW, 1>(a, sphi, PL, nullptr, 0, ty + 1, tx + 1,
                                        0, 0, g, m);
-      collide_stream<P, NP, false, WALL>(
-          a, m, hreg, perr, g, pp,
-          sup[(ty + G::UOY) * G::UW + tx + G::UOX],
-          sup[(G::UH + ty + G::UOY) * G::UW + tx + G::UOX], gx, gy);
+      collide_stream<P, NP, false, WALL>(a, m, hreg, perr, g, pp, upx, upy, gx, gy);
     }
+    if (ONEB) continue;
     // Every thread is done with this tile's stage and phi tile: refill the
     // stage with the tile S ahead.
     __syncthreads();
