@@ -610,6 +610,27 @@ __device__ __forceinline__ void collide_stream(
   const T C1 = T(3) * ff, D1 = T(9) * ff;
   const T E1 = T(3) * ff, E2 = T(4.5) * ff * a.jfac;
   const T keep_g = T(1) - tg;
+  // 16-bit forms: the writer's references, formed once per magnitude. Each
+  // c_k.u (as cdotu rounds it) is +-um[j] with um = ux, uy, ux + uy, uy - ux,
+  // and the rounded products 3 c.u, (c.u)^2 and (c.u) phi are odd or even in
+  // it, so every reference below has the bits of g_refp / adv_units at cdotu.
+  T um[4], g3u[4], g45[4];
+  const T uut = MIX ? __fmul_rn(T(-1.5), __fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy))) : T(0);
+  const T p3 = MIX ? __fmul_rn(pr, T(3) * a.sg_st) : T(0);
+  if constexpr (MIX) {
+    um[0] = ux;
+    um[1] = uy;
+    um[2] = cdotu(5, ux, uy);
+    um[3] = cdotu(6, ux, uy);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      g3u[j] = __fmul_rn(T(3), um[j]);
+      g45[j] = __fmul_rn(T(4.5), __fmul_rn(um[j], um[j]));
+    }
+  }
+  // index of c_k.u's magnitude in um, and its sign (k = 1..8)
+  auto mag = [](int k) { return (k == 1 || k == 3) ? 0 : ((k == 2 || k == 4) ? 1 : ((k == 5 || k == 7) ? 2 : 3)); };
+  auto sgn = [](int k) { return (k == 1 || k == 2 || k == 5 || k == 6) ? T(1) : T(-1); };
   T gv[9];
 #pragma unroll
   for (int k = 1; k < 9; ++k) {
@@ -621,10 +642,14 @@ __device__ __forceinline__ void collide_stream(
       inner += E1 * (cxk * m.grx + cyk * m.gry) + E2 * (cxk * m.Jx + cyk * m.Jy);
     const T t = A0 + C1 * cF + cu * inner;
     const int kk = dk[k];
-    if constexpr (MIX)  // relative to the equilibrium's parts at this node
-      gv[k] = keep_g * g[k] + a.sg_st * t -
-          g_refp(cdotu(kk, ux, uy), ux, uy, pr, a.rho_base * a.sg_st, T(3) * a.sg_st);
-    else
+    if constexpr (MIX) {  // relative to the equilibrium's parts at this node
+      // direction kk: k, or opp(k) (the same magnitude, the other sign)
+      const int j = mag(k);
+      const T sk = kk == k ? sgn(k) : -sgn(k);
+      const T sr = __fadd_rn(__fmul_rn(sk, g3u[j]), g45[j]);  // 3 c.u + 4.5 (c.u)^2
+      const T ref = __fadd_rn(__fmul_rn(__fadd_rn(sr, uut), a.rho_base * a.sg_st), p3);
+      gv[k] = keep_g * g[k] + a.sg_st * t - ref;
+    } else
       a.gm_out[(size_t)(kk - 1) * V + dst[k]] = keep_g * g[k] + w_of<T>(k) * t;
   }
   if constexpr (MIX) {  // converted two at a time
@@ -660,11 +685,13 @@ __device__ __forceinline__ void collide_stream(
       // relative to the advective part at this node (the slots' source),
       // converted two at a time; the mass balance uses each value as the
       // reader will decode it
-      T hv[9], rf[9];
+      T hv[9], rf[9], um3[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) um3[j] = adv_units(um[j], ph, T(3) * a.sh_st);
 #pragma unroll
       for (int k = 1; k < 9; ++k) {
         const T t = al + T(cx_of(k)) * bx + T(cy_of(k)) * by;
-        rf[k] = adv_units(cdotu(dk[k], ux, uy), ph, T(3) * a.sh_st);
+        rf[k] = __fmul_rn(dk[k] == k ? sgn(k) : -sgn(k), um3[mag(k)]);  // adv_units at cdotu(dk[k])
         hv[k] = keep * hreg[i][k] + t - rf[k];
       }
       typename Prec<P>::Sm sv[9];
